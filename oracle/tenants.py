@@ -1,0 +1,152 @@
+"""ctypes front end of the C tenant oracle (oracle/tenants.c). Test infrastructure.
+
+`build()` compiles tenants.c with the host C compiler (plain -O2, no FP
+contraction, no fast-math) into oracle/_build/liboracle_tenants.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tenants.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_tenants.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        L = C.c_int64
+        _lib.or_expf.argtypes = [C.c_float]; _lib.or_expf.restype = C.c_float
+        _lib.or_logf.argtypes = [C.c_float]; _lib.or_logf.restype = C.c_float
+        _lib.or_blackscholes.argtypes = [f32p] * 7 + [L]
+        _lib.or_gather.argtypes = [i32p, i32p, i32p, L, L]
+        _lib.or_gemm_f32.argtypes = [f32p, f32p, f32p, L, L, L]
+        _lib.or_gemm_f32_sample.argtypes = [f32p, f32p, i64p, i64p, f32p, L, L, L]
+        _lib.or_spmv_csr.argtypes = [i32p, i32p, f32p, f32p, f32p, f64p, f64p, L]
+        _lib.or_pchase.argtypes = [i32p, i32p, i32p, L, L]
+        _lib.or_triad.argtypes = [f32p, f32p, f32p, C.c_float, L, L]
+        _lib.or_hist256.argtypes = [u8p, u32p, L]
+        _lib.or_escape.argtypes = [u32p, L, L, L, C.c_float, C.c_float, C.c_float, C.c_float, L, L]
+        _lib.or_sort_u32.argtypes = [u32p, u32p, L]
+        _lib.or_matadd.argtypes = [f32p, f32p, f32p, L]
+    return _lib
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def expf(x: float) -> float:
+    return lib().or_expf(float(x))
+
+
+def logf(x: float) -> float:
+    return lib().or_logf(float(x))
+
+
+def blackscholes(S, K, r, v, T):
+    n = len(S)
+    call = np.empty(n, np.float32)
+    put = np.empty(n, np.float32)
+    lib().or_blackscholes(_c(S, np.float32), _c(K, np.float32), _c(r, np.float32),
+                          _c(v, np.float32), _c(T, np.float32), call, put, n)
+    return call, put
+
+
+def gather(a, idx, lo=0, hi=None, out=None):
+    n = len(idx)
+    hi = n if hi is None else hi
+    out = np.zeros(n, np.int32) if out is None else out
+    lib().or_gather(_c(a, np.int32), _c(idx, np.int32), out, lo, hi)
+    return out
+
+
+def gemm_f32(A, B):
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    Cm = np.empty((M, N), np.float32)
+    lib().or_gemm_f32(_c(A, np.float32), _c(B, np.float32), Cm, M, N, K)
+    return Cm
+
+
+def gemm_f32_sample(A, B, ii, jj):
+    M, K = A.shape
+    N = B.shape[1]
+    out = np.empty(len(ii), np.float32)
+    lib().or_gemm_f32_sample(_c(A, np.float32), _c(B, np.float32), _c(ii, np.int64),
+                             _c(jj, np.int64), out, len(ii), N, K)
+    return out
+
+
+def spmv_csr(rowptr, col, val, x):
+    n = len(rowptr) - 1
+    y32 = np.empty(n, np.float32)
+    y64 = np.empty(n, np.float64)
+    asum = np.empty(n, np.float64)
+    lib().or_spmv_csr(_c(rowptr, np.int32), _c(col, np.int32), _c(val, np.float32),
+                      _c(x, np.float32), y32, y64, asum, n)
+    return y32, y64, asum
+
+
+def pchase(nxt, start, hops):
+    end = np.empty(len(start), np.int32)
+    lib().or_pchase(_c(nxt, np.int32), _c(start, np.int32), end, len(start), hops)
+    return end
+
+
+def triad(b, c, s, lo=0, hi=None, out=None):
+    n = len(b)
+    hi = n if hi is None else hi
+    out = np.zeros(n, np.float32) if out is None else out
+    lib().or_triad(_c(b, np.float32), _c(c, np.float32), out, float(s), lo, hi)
+    return out
+
+
+def hist256(data):
+    h = np.empty(256, np.uint32)
+    lib().or_hist256(_c(data, np.uint8), h, len(data))
+    return h
+
+
+def escape(width, height, max_iter, x0, y0, dx, dy, row_lo=0, row_hi=None, out=None):
+    row_hi = height if row_hi is None else row_hi
+    out = np.zeros(width * height, np.uint32) if out is None else out
+    lib().or_escape(out, width, height, max_iter, float(x0), float(y0), float(dx), float(dy),
+                    row_lo, row_hi)
+    return out
+
+
+def sort_u32(data):
+    out = np.empty(len(data), np.uint32)
+    lib().or_sort_u32(_c(data, np.uint32), out, len(data))
+    return out
+
+
+def matadd(a, b):
+    n = a.shape[0]
+    c = np.empty((n, n), np.float32)
+    lib().or_matadd(_c(a, np.float32), _c(b, np.float32), c, n)
+    return c

@@ -1,0 +1,223 @@
+"""Pins for the Markov-model and scheduling oracle (oracle/markov.py,
+oracle/schedule.py, oracle/mcsim.py) against closed forms, an independent
+eigen-solver, a Monte Carlo simulation, brute force and the paper's Table 3."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import markov as mk
+from oracle import mcsim
+from oracle import schedule as sc
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+GPU = mk.GPUParams(n_sm=152, n_sched=4, f_sm_hz=1.9e9, dram_bytes_per_s=6753e9)
+
+
+def prof(R_m, L0=600.0, m_c=4.0, m_u=32.0, f_u=0.0, I=1000.0, name=""):
+    return mk.KernelProfile(R_m=R_m, L0=L0, m_c=m_c, m_u=m_u, f_u=f_u, I_block=I,
+                            warps_per_block=8, name=name)
+
+
+# --------------------------------------------------------------------- GTH
+
+def test_gth_two_state_closed_form():
+    for a, b in [(0.3, 0.1), (0.01, 0.9), (0.5, 0.5), (1e-6, 0.2)]:
+        P = np.array([[1 - a, a], [b, 1 - b]])
+        pi = mk.gth_stationary(P)
+        assert np.allclose(pi, [b / (a + b), a / (a + b)], rtol=1e-13, atol=0)
+
+
+def test_gth_against_eigensolver():
+    rng = np.random.default_rng(5)
+    for n in [3, 7, 20, 60]:
+        P = rng.random((n, n)) + 0.01
+        P /= P.sum(axis=1, keepdims=True)
+        pi = mk.gth_stationary(P)
+        w, v = np.linalg.eig(P.T)
+        k = int(np.argmin(np.abs(w - 1.0)))
+        ref = np.real(v[:, k])
+        ref /= ref.sum()
+        assert np.max(np.abs(pi - ref)) < 1e-12
+        assert np.max(np.abs(pi @ P - pi)) < 1e-13
+
+
+# --------------------------------------------------------------------- transition matrix
+
+@pytest.mark.parametrize("three", [False, True])
+def test_rows_are_distributions(three):
+    pA = prof(0.2, f_u=0.3)
+    pB = prof(0.05, L0=300.0, f_u=0.6)
+    for profiles, warps in [([pA], [6]), ([pA, pB], [3, 5]), ([pB, pA], [1, 2])]:
+        _, pi, joint, P = mk.model_ipc(profiles, warps, GPU, three_state=three)
+        assert np.all(P >= 0.0)
+        assert np.max(np.abs(P.sum(axis=1) - 1.0)) < 1e-13
+        assert abs(pi.sum() - 1.0) < 1e-13
+
+
+def test_homogeneous_single_warp_closed_form():
+    # W = 1: states {ready, idle}; ready -> idle w.p. R_m, idle -> ready w.p. q = min(1, 1/L)
+    # with L = L0 + b0 + a0 m I / B_v at I = 1, so IPC = q / (q + R_m) = 1 / (1 + R_m L)
+    for R_m, L0 in [(0.1, 600.0), (0.5, 50.0), (0.02, 1000.0)]:
+        p = prof(R_m, L0=L0)
+        L = L0 + GPU.b0 + GPU.a0 * p.m_c * 1 / GPU.B_v
+        assert abs(mk.homogeneous_ipc(p, 1, GPU) - 1.0 / (1.0 + R_m * L)) < 1e-13
+
+
+def test_homogeneous_no_memory_is_full_issue():
+    assert abs(mk.homogeneous_ipc(prof(0.0), 8, GPU) - 1.0) < 1e-13
+
+
+def test_homogeneous_monotone():
+    ipcs = [mk.homogeneous_ipc(prof(r), 8, GPU) for r in [0.01, 0.05, 0.1, 0.2, 0.4]]
+    assert all(b <= a + 1e-15 for a, b in zip(ipcs, ipcs[1:]))
+    ipcs = [mk.homogeneous_ipc(prof(0.1, L0=l), 8, GPU) for l in [100, 300, 600, 1200]]
+    assert all(b <= a + 1e-15 for a, b in zip(ipcs, ipcs[1:]))
+    # more warps hide more latency
+    ipcs = [mk.homogeneous_ipc(prof(0.05, L0=400), w, GPU) for w in [1, 2, 4, 8]]
+    assert all(b >= a - 1e-15 for a, b in zip(ipcs, ipcs[1:]))
+
+
+def test_heterogeneous_reduces_to_homogeneous():
+    p = prof(0.12)
+    q = prof(0.3, L0=200)
+    (a, b), _, _, _ = mk.model_ipc([p, q], [6, 0], GPU)
+    assert abs(a - mk.homogeneous_ipc(p, 6, GPU)) < 1e-14 and b == 0.0
+
+
+def test_identical_kernels_lump_and_split():
+    # two copies of one kernel: the pair chain lumps onto the homogeneous chain
+    # with W = wA + wB, and the issue rate splits wA : wB (exchangeable warps)
+    p = prof(0.08, L0=500)
+    (a, b), _, _, _ = mk.model_ipc([p, p], [3, 5], GPU)
+    h = mk.homogeneous_ipc(p, 8, GPU)
+    assert abs((a + b) - h) < 1e-13
+    assert abs(a / (a + b) - 3 / 8) < 1e-12
+
+
+def test_swap_symmetry():
+    p, q = prof(0.2, L0=700), prof(0.03, L0=250, f_u=0.5)
+    for three in (False, True):
+        (a, b), _, _, _ = mk.model_ipc([p, q], [2, 6], GPU, three)
+        (c, d), _, _, _ = mk.model_ipc([q, p], [6, 2], GPU, three)
+        assert abs(a - d) < 1e-13 and abs(b - c) < 1e-13
+
+
+def test_three_state_lumps_when_classes_equal():
+    # with equal sector counts the coalesced/uncoalesced split is invisible
+    p3 = prof(0.15, m_c=8.0, m_u=8.0, f_u=0.4)
+    p2 = prof(0.15, m_c=8.0, m_u=8.0, f_u=0.0)
+    assert abs(mk.homogeneous_ipc(p3, 5, GPU, True) - mk.homogeneous_ipc(p2, 5, GPU, False)) < 1e-13
+    # and uncoalesced traffic lowers IPC
+    pu = prof(0.15, m_c=4.0, m_u=32.0, f_u=0.4)
+    assert mk.homogeneous_ipc(pu, 5, GPU, True) < mk.homogeneous_ipc(p2, 5, GPU, False)
+
+
+@pytest.mark.parametrize("case", [
+    ([dict(R_m=0.1, L0=300)], [4], False),
+    ([dict(R_m=0.3, L0=150), dict(R_m=0.02, L0=600)], [3, 3], False),
+    ([dict(R_m=0.2, L0=200, f_u=0.5)], [3], True),
+])
+def test_chain_matches_monte_carlo(case):
+    profs, warps, three = case
+    P = [prof(**d) for d in profs]
+    ipc, _, _, _ = mk.model_ipc(P, warps, GPU, three)
+    sim, se = mcsim.simulate_ipc(P, warps, GPU, rounds=3000, replicas=1000, burn_in=300,
+                                 seed=11, three_state=three)
+    for a, b, s in zip(ipc, sim, se):
+        assert abs(a - b) < 4 * s + 2e-4, (a, b, s)
+
+
+def test_cp_closed_forms():
+    assert abs(mk.cp([0.5, 0.25], [1.0, 0.5])) < 1e-15          # half speed each: no profit
+    assert abs(mk.cp([1.0, 0.5], [1.0, 0.5]) - 0.5) < 1e-15     # both at full speed: 1/2
+
+
+def test_balanced_ratio_minimises_dT():
+    pA, pB = prof(0.25, L0=700, I=5000), prof(0.01, L0=300, I=800)
+    best, evals, (ia, ib) = mk.evaluate_pair(pA, pB, 4, GPU)
+    assert len(evals) == 3 and {(e.bA, e.bB) for e in evals} == {(1, 3), (2, 2), (3, 1)}
+    assert best.dT == min(e.dT for e in evals)
+    for e in evals:
+        assert abs(e.dT - abs(pA.I_block * e.bA * GPU.n_sm / e.cipcA
+                              - pB.I_block * e.bB * GPU.n_sm / e.cipcB)) < 1e-9 * e.dT + 1e-9
+        assert 0.0 < e.cipcA <= ia + 1e-12 and 0.0 < e.cipcB <= ib + 1e-12
+
+
+# --------------------------------------------------------------------- pruning (Table 3)
+
+def _read_table():
+    rows = [l.split() for l in open(os.path.join(GOLD, "c2050_pur_mur.txt")) if not l.startswith("#")]
+    pur = [float(r[1]) for r in rows]
+    mur = [float(r[2]) for r in rows]
+    lines = [l.split() for l in open(os.path.join(GOLD, "c2050_pruning_table.txt")) if not l.startswith("#")]
+    aps = [float(x) for x in lines[0][1:]]
+    table = [(float(l[0]), [int(x) for x in l[1:]]) for l in lines[1:]]
+    return pur, mur, aps, table
+
+
+def test_pruning_reproduces_table3():
+    pur, mur, aps, table = _read_table()
+    exact = 0
+    for am, counts in table:
+        for ap, want in zip(aps, counts):
+            got = sc.count_pruned(pur, mur, ap, am)
+            # every cell within 3 and never above the printed count
+            assert want - 3 <= got <= want
+            exact += got == want
+        if am <= 0.045:
+            assert [sc.count_pruned(pur, mur, ap, am) for ap in aps] == counts
+    assert exact >= 78
+    # the literal "or" reading does not reproduce the table
+    n = len(pur)
+    or_exact = sum(
+        sum(1 for i in range(n) for j in range(i + 1, n)
+            if abs(pur[i] - pur[j]) < ap or abs(mur[i] - mur[j]) < am) == want
+        for am, counts in table for ap, want in zip(aps, counts))
+    assert or_exact <= 2
+
+
+def test_prune_all_falls_back():
+    ts = [sc.Tenant(prof(0.1), 10, PUR=0.5, MUR=0.1) for _ in range(3)]
+    pairs = [(0, 1), (0, 2), (1, 2)]
+    assert sc.prune_pairs(pairs, ts, 1.0, 1.0) == pairs
+    ts[2].PUR = 0.0
+    assert sc.prune_pairs(pairs, ts, 0.2, 1.0) == [(0, 2), (1, 2)]
+
+
+# --------------------------------------------------------------------- greedy vs brute force
+
+def _mix(seed, n):
+    rng = np.random.default_rng(seed)
+    kinds = [prof(0.30, L0=800, I=400, name="mem"), prof(0.02, L0=300, I=3000, name="alu"),
+             prof(0.10, L0=500, I=1200, name="mid"), prof(0.20, L0=600, f_u=0.5, I=600, name="unc")]
+    return [sc.Tenant(kinds[int(rng.integers(4))], int(rng.integers(50, 400))) for _ in range(n)]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_greedy_is_feasible_and_not_below_optimum(seed):
+    ts = _mix(seed, 4)
+    model = sc.PairModel(GPU, 4)
+    phases, greedy = sc.greedy_plan(ts, model)
+    opt = sc.brute_force(ts, model)
+    assert greedy >= opt * (1 - 1e-12)
+    # every kernel's blocks are fully scheduled once
+    done = np.zeros(len(ts))
+    for cs, dur in phases:
+        done[cs.A] += dur * cs.cipcA * GPU.n_sm / ts[cs.A].prof.I_block
+        if cs.B is not None:
+            done[cs.B] += dur * cs.cipcB * GPU.n_sm / ts[cs.B].prof.I_block
+    assert np.allclose(done, [t.blocks for t in ts], rtol=1e-9)
+    mc = sc.monte_carlo(ts, model, 30, seed=seed)
+    assert np.all(mc >= opt * (1 - 1e-12))
+
+
+def test_findcoschedule_tie_break_and_solo():
+    model = sc.PairModel(GPU, 4)
+    p = prof(0.1)
+    ts = [sc.Tenant(p, 10) for _ in range(3)]
+    cs = sc.find_coschedule([2, 0, 1], ts, model)
+    assert (cs.A, cs.B) == (0, 1)                 # equal CP everywhere: smallest pair
+    cs = sc.find_coschedule([2], ts, model)
+    assert cs.B is None and cs.bA == 4
