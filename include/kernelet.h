@@ -1,0 +1,365 @@
+/*
+ * kernelet.h — C ABI of a GB300 (sm_103a) runtime for sliced, co-scheduled
+ * execution of concurrently submitted GPU kernels ("Kernelet", Zhong & He,
+ * arXiv 1303.5164).
+ *
+ * Problem statement (Section 2.2): tenants submit kernels; a kernel is k thread
+ * blocks with IDs 0..k-1 that do not depend on one another (assumption 2); a
+ * slice is a contiguous range of block IDs; a co-schedule runs slices of two
+ * kernels at the same time; the goal is the minimum total execution time of the
+ * pending kernels, re-optimised on the residuals when kernels arrive.
+ *
+ * How this library realises it on one GPU:
+ *   - kl_submit copies a kernel descriptor (type, grid, block, resources,
+ *     arguments) into the pending set R (Algorithm 1, "a new kernel comes").
+ *   - kl_launch starts ONE persistent co-scheduler kernel over R: every SM
+ *     holds `slots` CTAs; for the current co-schedule <K1,K2,size1,size2>
+ *     (Algorithm 1) the first size1 slots of each SM run K1 and the other size2
+ *     run K2; each CTA pulls a slice (contiguous block range) with one atomic
+ *     and runs it with rectified block indices (Section 4.1, index
+ *     rectification). When a kernel has handed out its last block the CTA that
+ *     sees it re-plans on the device (FindCoSchedule over the pending set, using
+ *     the CP table the Markov model of Section 4.4 computed on the host).
+ *   - kl_poll / kl_wait / kl_drain report completion.
+ *   - kl_model_* and kl_plan are pure host functions: the performance model
+ *     (Section 4.4), pruning (Section 4.3) and the greedy plan (Algorithm 1).
+ *
+ * Conventions for every function:
+ *   - Return value: KL_OK (0) or a negative kl_status. Nothing is thrown
+ *     across the ABI; no function aborts the process.
+ *   - Pointers inside kl_args_* blocks are DEVICE pointers the caller owns
+ *     (allocated e.g. with torch). They must stay valid and untouched until the
+ *     tenant's handle is DONE or ERROR. All other pointers are host pointers.
+ *   - Thread safety: one kl_runtime may be used from several host threads;
+ *     calls on it are serialised by an internal mutex. Pure functions are
+ *     reentrant.
+ *   - Device-side waits are bounded (kl_config.device_wait_limit_ns); an
+ *     expired wait ends the run with KL_EDEVICE_TIMEOUT and leaves the context
+ *     usable.
+ */
+#ifndef KERNELET_H
+#define KERNELET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KL_ABI_VERSION 1
+#define KL_BLOCK_THREADS 256     /* every tenant block has 256 threads          */
+#define KL_MAX_ARGS_BYTES 96     /* largest kl_args_* block                     */
+#define KL_MAX_SLOTS 8           /* per-SM block slots of the co-scheduler      */
+
+typedef enum {
+    KL_OK = 0,
+    KL_EINVAL = -1,           /* bad argument, descriptor or size              */
+    KL_ENOMEM = -2,           /* host or device allocation failed              */
+    KL_EAGAIN = -3,           /* queue full / a run is still in flight         */
+    KL_ETIMEDOUT = -4,        /* host-side wait expired (work continues)       */
+    KL_ECUDA = -5,            /* a CUDA runtime call failed                    */
+    KL_EDEVICE_TIMEOUT = -6,  /* a device-side bounded wait expired            */
+    KL_ESTATE = -7,           /* call not valid in the current state           */
+    KL_ENOTFOUND = -8,        /* unknown handle                                */
+    KL_EOVERFLOW = -9         /* a device table (phases, tenants) overflowed   */
+} kl_status;
+
+typedef enum { KL_PENDING = 0, KL_RUNNING = 1, KL_DONE = 2, KL_ERROR = 3 } kl_state;
+
+typedef struct kl_runtime kl_runtime;   /* opaque; owned by the library */
+
+/* Tenant kernel types. Each is a hand-written device function that runs one
+ * 256-thread block given its rectified (virtual) block index. */
+typedef enum {
+    KL_T_GATHER = 0,        /* out[i] = a[idx[i]], int32                           */
+    KL_T_BLACKSCHOLES = 1,  /* European call/put, binary32                         */
+    KL_T_GEMM_F32 = 2,      /* C = A B, binary32, ascending-k fused chain per C[i][j] */
+    KL_T_SPMV_CSR = 3,      /* y = A x, CSR, binary32                              */
+    KL_T_PCHASE = 4,        /* end[t] = next^hops(start[t]), int32                 */
+    KL_T_TRIAD = 5,         /* a = s*c + b (fused), binary32                       */
+    KL_T_HIST256 = 6,       /* 256-bin histogram of bytes, uint32 counts            */
+    KL_T_ESCAPE = 7,        /* escape-time iteration count per pixel, uint32       */
+    KL_T_BITONIC = 8,       /* ascending bitonic sort of 2^log2n uint32 keys        */
+    KL_T_MATADD = 9,        /* c = a + b on an n x n matrix, 16x16 blocks (Section 4.1 example) */
+    KL_T_COUNT = 10
+} kl_tenant_type;
+
+/* ----------------------------------------------------------- tenant arguments
+ * Layouts: row-major, densely packed, element types as named. Pointers to
+ * arrays that the tenant reads or writes with 16-byte vector accesses must be
+ * 16-byte aligned (marked "16B"). */
+
+typedef struct {            /* KL_T_GATHER: 1024 elements per block           */
+    const int32_t* a;       /* [n_src]                                         */
+    const int32_t* idx;     /* [n] 16B, values in [0, n_src)                   */
+    int32_t* out;           /* [n] 16B                                         */
+    uint64_t n;
+} kl_args_gather;
+
+typedef struct {            /* KL_T_BLACKSCHOLES: 256 options per block       */
+    const float *S, *K, *r, *v, *T;   /* [n] spot, strike, rate, volatility, years */
+    float *call, *put;                /* [n]                                   */
+    uint64_t n;
+} kl_args_blackscholes;
+
+typedef struct {            /* KL_T_GEMM_F32: one 128x64 tile of C per block  */
+    const float* A;         /* [M][K] 16B                                      */
+    const float* B;         /* [K][N] 16B                                      */
+    float* C;               /* [M][N] 16B                                      */
+    uint32_t M, N, K;       /* N and K multiples of 4                          */
+    uint32_t pad;
+} kl_args_gemm_f32;
+
+typedef struct {            /* KL_T_SPMV_CSR: 32 rows per block                */
+    const int32_t* rowptr;  /* [nrows+1], non-decreasing, rowptr[0] = 0        */
+    const int32_t* col;     /* [nnz] values in [0, ncols)                      */
+    const float* val;       /* [nnz]                                           */
+    const float* x;         /* [ncols]                                         */
+    float* y;               /* [nrows]                                         */
+    uint32_t nrows, ncols;
+} kl_args_spmv_csr;
+
+typedef struct {            /* KL_T_PCHASE: 256 chasers per block              */
+    const int32_t* next;    /* [N] values in [0, N)                            */
+    const int32_t* start;   /* [nchasers] values in [0, N)                     */
+    int32_t* end;           /* [nchasers]                                      */
+    uint32_t N, nchasers, hops, pad;
+} kl_args_pchase;
+
+typedef struct {            /* KL_T_TRIAD: 4096 elements per block             */
+    const float* b;         /* [n] 16B                                         */
+    const float* c;         /* [n] 16B                                         */
+    float* a;               /* [n] 16B                                         */
+    float s;
+    uint32_t pad;
+    uint64_t n;
+} kl_args_triad;
+
+typedef struct {            /* KL_T_HIST256: stage 0 = 1 block clears hist;    */
+    const uint8_t* data;    /* [n] 16B   stage 1 = 16384 bytes per block        */
+    uint32_t* hist;         /* [256]                                           */
+    uint64_t n;
+} kl_args_hist256;
+
+typedef struct {            /* KL_T_ESCAPE: 256 pixels (row-major) per block   */
+    uint32_t* count;        /* [height][width]                                 */
+    uint32_t width, height, max_iter, pad;
+    float x0, y0, dx, dy;   /* pixel (i,j) -> c = (x0+(j+.5)dx, y0+(i+.5)dy)    */
+} kl_args_escape;
+
+typedef struct {            /* KL_T_BITONIC: 4096-key tiles; stage 0 reads in, */
+    const uint32_t* in;     /* [2^log2n]   later stages work in place on out   */
+    uint32_t* out;          /* [2^log2n]                                       */
+    uint32_t log2n;         /* 1..30                                           */
+    uint32_t pad;
+} kl_args_bitonic;
+
+typedef struct {            /* KL_T_MATADD: 16x16-thread blocks, (n/16)^2 grid */
+    const float* a;
+    const float* b;
+    float* c;
+    uint32_t n;             /* multiple of 16                                  */
+    uint32_t pad;
+} kl_args_matadd;
+
+/* Launch shape of a tenant as a plain kernel would use it (Section 2.2: a
+ * kernel is k thread blocks). Multi-stage tenants (histogram, bitonic sort)
+ * are a chain of grids; stage s may start only when stage s-1 has finished. */
+typedef struct {
+    uint32_t grid[3];       /* blocks of stage 0 (x, y, z)                      */
+    uint32_t block[3];      /* {256, 1, 1}                                      */
+    uint32_t nstages;
+    uint32_t smem_bytes;    /* dynamic shared memory per block                  */
+    uint64_t total_blocks;  /* summed over stages                               */
+} kl_tenant_shape;
+
+/* Descriptor of one submitted kernel. */
+typedef struct {
+    uint32_t type;              /* kl_tenant_type                                */
+    uint32_t grid[3];           /* must equal kl_tenant_shape().grid             */
+    uint32_t block[3];          /* must be {256, 1, 1}                           */
+    uint32_t smem_bytes;        /* resource profile: declared dynamic smem       */
+    uint32_t regs_per_thread;   /* resource profile: declared registers (0 = n/a) */
+    uint32_t slice_blocks;      /* blocks per slice; 0 = runtime's per-type size */
+    const void* args;           /* -> kl_args_<type> (host memory; copied)        */
+    uint32_t args_size;         /* sizeof(kl_args_<type>)                        */
+    uint32_t flags;             /* reserved, 0                                   */
+    uint64_t footprint_bytes;   /* device bytes the kernel touches (admission)   */
+} kl_kernel_desc;
+
+typedef uint64_t kl_handle;     /* 0 is never a valid handle */
+
+typedef enum {
+    KL_RATIO_BALANCED = 0,      /* min dT (Eq. executiontime), ties -> max CP     */
+    KL_RATIO_MAX_CP = 1,        /* max CP over the feasible splits                */
+    KL_RATIO_FIXED = 2          /* kl_config.fixed_slots_a slots for K1           */
+} kl_ratio_policy;
+
+typedef struct {
+    int32_t device;                 /* CUDA ordinal (default 0)                     */
+    uint32_t slots_per_sm;          /* co-scheduler CTAs per SM; 0 = occupancy limit */
+    uint32_t max_tenants;           /* pending-set capacity per run (default 4096)  */
+    uint32_t model_states;          /* 2 or 3 (uncoalesced extension); default 3    */
+    uint32_t ratio_policy;          /* kl_ratio_policy                              */
+    uint32_t fixed_slots_a;         /* for KL_RATIO_FIXED                           */
+    uint64_t device_wait_limit_ns;  /* bound on every device spin (default 2 s)     */
+    uint64_t mem_cap_bytes;         /* admission cap on summed footprints (0 = none) */
+    double alpha_p, alpha_m;        /* pruning thresholds; negative = no pruning    */
+    uint32_t flags;                 /* reserved, 0                                  */
+    uint32_t reserved;
+} kl_config;
+
+/* Model inputs for one tenant type (Table 1 parameters, measured by profiling
+ * a plain launch of the kernel, Section 4.4 "getting the input"). */
+typedef struct {
+    double R_m;             /* memory instructions / instructions                */
+    double f_u;             /* fraction of memory instructions that are uncoalesced */
+    double m_c;             /* DRAM sectors per coalesced memory instruction     */
+    double m_u;             /* DRAM sectors per uncoalesced memory instruction   */
+    double L0;              /* unloaded memory latency, SM cycles                */
+    double I_block;         /* warp instructions per thread block                */
+    double PUR, MUR;        /* Section 4.3 utilisation ratios (pruning)          */
+    uint32_t warps_per_block;
+    uint32_t valid;         /* 0 = no profile for this type                      */
+} kl_profile;
+
+typedef struct {
+    uint32_t n_sm;          /* SMs                                               */
+    uint32_t n_sched;       /* warp schedulers per SM (virtual-SM divisor)       */
+    double f_sm_hz;         /* SM clock used to convert cycles to seconds        */
+    double dram_bytes_per_s;
+    double sector_bytes;    /* DRAM access granularity (32)                      */
+    double a0, b0;          /* linear latency model parameters                   */
+} kl_model_params;
+
+typedef struct {
+    int32_t A, B;           /* submit indices; B = -1 for a solo phase; A = -1 ends */
+    uint32_t slots_a, slots_b;
+    double cp;              /* predicted co-scheduling profit (Eq. cp)           */
+    uint64_t t_ns;          /* device globaltimer when the phase was published   */
+    int32_t trigger;        /* tenant whose exhaustion ended the previous phase  */
+    uint32_t n_pending;     /* kernels with blocks left when the phase was chosen */
+    uint64_t pending_mask;  /* bit i: kernel i (i < 64) was pending               */
+} kl_phase;
+
+typedef struct {
+    int32_t state;              /* kl_state                                      */
+    int32_t error;              /* kl_status when state == KL_ERROR               */
+    uint64_t t_submit_ns;       /* host steady clock at kl_submit                 */
+    uint64_t t_start_ns;        /* device: first slice of this kernel started     */
+    uint64_t t_end_ns;          /* device: last block finished                    */
+    uint64_t t_launch_ns;       /* device: run start (first CTA)                  */
+    uint32_t slices;            /* slices pulled                                  */
+    uint32_t blocks;            /* blocks executed                                */
+} kl_tenant_stats;
+
+typedef struct {
+    uint32_t n_tenants;
+    uint32_t n_phases;
+    int32_t error;              /* kl_status of the run                           */
+    uint32_t slots_per_sm;
+    uint32_t grid_ctas;
+    uint32_t pad;
+    uint64_t t_launch_ns;       /* device globaltimer at the first CTA            */
+    uint64_t t_end_ns;          /* device globaltimer at the last completion      */
+} kl_run_stats;
+
+typedef enum { KL_BASE_SERIAL = 0, KL_BASE_MULTISTREAM = 1 } kl_baseline_mode;
+
+/* ------------------------------------------------------------------ runtime */
+
+/* Fill `cfg` with defaults. */
+int kl_config_default(kl_config* cfg);
+
+/* Create a runtime on cfg->device that launches on `cuda_stream` (a
+ * cudaStream_t, may be NULL for the legacy default stream). Allocates the
+ * device queue (cfg->max_tenants descriptors) and pinned host staging. */
+int kl_create(const kl_config* cfg, void* cuda_stream, kl_runtime** out);
+
+/* Wait for in-flight work (up to the device wait limit), free everything.
+ * KL_ESTATE if a run could not be retired. */
+int kl_destroy(kl_runtime* rt);
+
+/* Launch shape of a tenant (no device work). */
+int kl_tenant_shape_of(uint32_t type, const void* args, uint32_t args_size, kl_tenant_shape* out);
+
+/* Add a kernel to the pending set. Validates type, grid/block against the
+ * tenant's shape, alignment, and admission (summed footprint <= mem cap).
+ * Non-blocking; copies the descriptor and arguments. KL_EAGAIN when the
+ * pending set is full or over the memory cap. */
+int kl_submit(kl_runtime* rt, const kl_kernel_desc* desc, kl_handle* out);
+
+/* Plan and start the pending set as one persistent co-scheduled launch on the
+ * runtime's stream; returns without waiting. KL_EAGAIN if a run is in flight. */
+int kl_launch(kl_runtime* rt);
+
+/* Execute the pending set with plain kernel launches instead of the
+ * co-scheduler: KL_BASE_SERIAL = one stream in submit order; KL_BASE_MULTISTREAM
+ * = tenant i on stream i % nstreams (concurrent kernel execution). The runtime
+ * stream is forked into the side streams and joined back, so events recorded
+ * on it bracket the whole run. Returns without waiting. */
+int kl_launch_baseline(kl_runtime* rt, int mode, uint32_t nstreams);
+
+/* Current state of a handle (kl_state) without blocking. */
+int kl_poll(kl_runtime* rt, kl_handle h, int* state);
+
+/* Block until the handle is DONE/ERROR or timeout_ns elapses (KL_ETIMEDOUT). */
+int kl_wait(kl_runtime* rt, kl_handle h, uint64_t timeout_ns);
+
+/* Launch whatever is pending, then wait for the whole run; returns the run's
+ * status (KL_OK, KL_EDEVICE_TIMEOUT, ...). */
+int kl_drain(kl_runtime* rt, uint64_t timeout_ns);
+
+int kl_get_stats(kl_runtime* rt, kl_handle h, kl_tenant_stats* out);
+int kl_get_run_stats(kl_runtime* rt, kl_run_stats* out);
+
+/* Phase log (the co-schedules the device chose) of the last retired run. */
+int kl_get_phases(kl_runtime* rt, kl_phase* out, uint32_t cap, uint32_t* n);
+
+/* Model inputs: per-type profiles and GPU parameters. Changing them
+ * invalidates the cached CP table. */
+int kl_set_profiles(kl_runtime* rt, const kl_profile* profiles, uint32_t n_types);
+int kl_set_model_params(kl_runtime* rt, const kl_model_params* params);
+int kl_get_model_params(kl_runtime* rt, kl_model_params* out);
+
+/* CP table the device planner uses: cp[i*KL_T_COUNT+j] and slots for the
+ * first kernel of a (type i, type j) pair at `slots` slots per SM. */
+int kl_get_cp_table(kl_runtime* rt, double* cp, uint32_t* slots_a, uint8_t* allowed);
+
+/* ------------------------------------------------------------ pure functions */
+
+/* Per-kernel IPC (per SM = virtual-SM IPC x n_sched) of n kernels sharing a
+ * virtual SM with warps[k] warps of kernel k (Eqs. modelIPC, ipc_k1, ipc_k2).
+ * model_states 2 or 3. At most 4 kernels and 4096 joint states. */
+int kl_model_ipc(const kl_model_params* gp, const kl_profile* profiles, const uint32_t* warps,
+                 uint32_t n, uint32_t model_states, double* ipc_out);
+
+/* Evaluate every split (a + b = slots, a, b >= 1) of a pair: concurrent IPCs,
+ * CP (Eq. cp) and dT (Eq. executiontime), and the split chosen by `policy`.
+ * Arrays have slots-1 entries, index a-1. solo_ipc[2] = IPC alone at `slots`. */
+int kl_model_pair(const kl_model_params* gp, const kl_profile* pa, const kl_profile* pb,
+                  uint32_t slots, uint32_t model_states, uint32_t policy, uint32_t fixed_a,
+                  double* cipc_a, double* cipc_b, double* cp, double* dT, double* solo_ipc,
+                  uint32_t* best_a);
+
+/* Greedy plan (Algorithm 1) of n kernels with types[i] and blocks[i] thread
+ * blocks, all pending at time 0, simulated with the model's rates. Writes up
+ * to cap phases and the predicted makespan in SM cycles. */
+int kl_plan(const kl_model_params* gp, const kl_profile* type_profiles, uint32_t n_types,
+            const uint32_t* types, const uint64_t* blocks, uint32_t n, uint32_t slots,
+            uint32_t model_states, uint32_t policy, double alpha_p, double alpha_m,
+            kl_phase* phases, double* phase_cycles, uint32_t cap, uint32_t* n_phases,
+            double* makespan_cycles);
+
+/* Number of pairs of n kernels removed by the pruning rule (Section 4.3). */
+int kl_count_pruned(const double* pur, const double* mur, uint32_t n, double alpha_p,
+                    double alpha_m, uint32_t* out);
+
+const char* kl_strerror(int code);
+int kl_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KERNELET_H */

@@ -258,9 +258,26 @@ def evaluate_pair(pA: KernelProfile, pB: KernelProfile, slots: int, gpu: GPUPara
         evals.append(PairEval(bA, bB, cA, cB, cp([cA, cB], [ipcA, ipcB]), dT))
     best = None
     for e in evals:
-        if best is None:
-            best = e
-            continue
-        if e.dT < best.dT or (e.dT == best.dT and (e.cp > best.cp or (e.cp == best.cp and e.bA > best.bA))):
+        if best is None or better_split(e, best):
             best = e
     return best, evals, (ipcA, ipcB)
+
+
+CP_TIE = 1e-12      # CP values closer than this are equal
+DT_TIE = 1e-9       # dT values closer than this (relative) are equal
+
+
+def better_split(e: "PairEval", best: "PairEval", policy: str = "balanced") -> bool:
+    """Order of slot splits. The paper picks the split with the smallest dT
+    (Eq. executiontime) and states no tie rule; ties (within rounding) go to
+    the larger CP, then the more even split, then the larger share of K1."""
+    if policy == "balanced":
+        scale = max(e.dT, best.dT)
+        if abs(e.dT - best.dT) > DT_TIE * scale:
+            return e.dT < best.dT
+    if abs(e.cp - best.cp) > CP_TIE:
+        return e.cp > best.cp
+    ue, ub = abs(e.bA - e.bB), abs(best.bA - best.bB)
+    if ue != ub:
+        return ue < ub
+    return e.bA > best.bA

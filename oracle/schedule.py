@@ -8,7 +8,8 @@
 * FindCoSchedule (Algorithm 1, procedure): enumerate the N(N-1)/2 pairs of
   pending kernels, prune, evaluate CP of each survivor at its balanced slice
   ratio with the performance model, return the pair with the largest CP
-  (ties: smallest (i, j) in submission order). One pending kernel runs alone.
+  (CP equal within 1e-12: smallest (i, j) in submission order). One pending
+  kernel runs alone.
 * Greedy loop (Algorithm 1, main): repeat the chosen co-schedule while the
   pending set is unchanged AND both kernels still have thread blocks; then
   re-plan on the residuals.
@@ -23,7 +24,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .markov import GPUParams, KernelProfile, evaluate_pair, homogeneous_ipc, warps_on_virtual_sm
+from .markov import CP_TIE, GPUParams, KernelProfile, evaluate_pair, homogeneous_ipc, warps_on_virtual_sm
 
 
 @dataclass
@@ -95,9 +96,9 @@ def find_coschedule(R, tenants, model: PairModel, alpha_p=None, alpha_m=None) ->
     pairs = [(R[x], R[y]) for x in range(len(R)) for y in range(x + 1, len(R))]
     cand = prune_pairs(pairs, tenants, alpha_p, alpha_m)
     best = None
-    for (i, j) in cand:
+    for (i, j) in cand:          # ascending (i, j): a CP tie keeps the earlier pair
         ev, _, _ = model.pair(tenants[i].prof, tenants[j].prof)
-        if best is None or ev.cp > best.cp:
+        if best is None or ev.cp > best.cp + CP_TIE:
             best = CoSchedule(i, j, ev.bA, ev.bB, ev.cp, ev.cipcA, ev.cipcB)
     return best
 

@@ -1,0 +1,71 @@
+// Internal layouts shared by the host runtime (kl_runtime.cpp) and the device
+// code (kl_cosched.cu, kl_native.cu). Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+#include "kernelet.h"
+
+namespace kl {
+
+constexpr int kThreads = KL_BLOCK_THREADS;
+constexpr int kMaxSM = 256;
+constexpr int kNoTenant = -1;
+
+// One submitted kernel in device memory (128-byte aligned, 256 bytes).
+// Static fields are written by the host before the launch; dynamic fields are
+// zero at launch and owned by the device during the run.
+struct alignas(128) TenantDev {
+  // ---- static
+  uint32_t type;          // kl_tenant_type
+  uint32_t slice;         // blocks per slice (pull granularity)
+  uint32_t total;         // thread blocks summed over stages
+  uint32_t nstages;
+  uint32_t index;         // submit index within the run
+  uint32_t pad0[3];
+  alignas(16) unsigned char args[KL_MAX_ARGS_BYTES];
+  // ---- dynamic (own 128-byte line, away from the arguments)
+  alignas(128) uint32_t next;     // next block to hand out (cumulative over stages)
+  uint32_t done;                  // blocks finished (cumulative over stages)
+  uint32_t drained;               // 1 once every block has been handed out
+  uint32_t status;                // kl_state
+  uint32_t slices;                // slices pulled
+  uint32_t pad1;
+  unsigned long long t_start;     // globaltimer of the first pulled slice
+  unsigned long long t_end;       // globaltimer when the last block finished
+};
+static_assert(sizeof(TenantDev) == 256, "TenantDev layout");
+
+struct PhaseDev {
+  int32_t A, B;             // tenant indices; B < 0 solo; A < 0 = end of run
+  uint32_t slots_a, slots_b;
+  double cp;
+  unsigned long long t;
+  int32_t trigger;
+  uint32_t n_pending;          // kernels with blocks left when the phase was chosen
+  unsigned long long pending;  // bit i: kernel i (i < 64) was pending
+};
+static_assert(sizeof(PhaseDev) == 48, "PhaseDev layout");
+
+// Run-wide state of one co-scheduled launch.
+struct alignas(128) RunDev {
+  // ---- static (host-written)
+  uint32_t n_tenants;
+  uint32_t slots;              // CTAs per SM
+  uint32_t max_phases;
+  uint32_t n_types;
+  unsigned long long wait_limit_ns;
+  double cp[KL_T_COUNT][KL_T_COUNT];          // CP of (type row as K1, type col as K2)
+  uint32_t slots_a[KL_T_COUNT][KL_T_COUNT];   // slots of the K1 (row) kernel
+  uint32_t allowed[KL_T_COUNT][KL_T_COUNT];   // 1 = pair survives pruning
+  // ---- dynamic (zero at launch)
+  alignas(128) uint32_t phase_seq;   // index of the published phase
+  uint32_t phase_claim;              // == phase_seq unless a re-plan is in progress
+  uint32_t n_complete;               // tenants finished
+  int32_t error;                     // first kl_status error
+  uint32_t error_info;
+  uint32_t ctas_done;
+  unsigned long long t_launch;       // globaltimer, first CTA
+  unsigned long long t_end;          // globaltimer, last completion
+  alignas(128) uint32_t sm_ticket[kMaxSM];
+};
+
+}  // namespace kl

@@ -1,0 +1,800 @@
+// Host runtime behind the C ABI: the pending set R, admission, the CP table
+// the device planner reads, launch of the persistent co-scheduler (or of the
+// plain-launch baselines), completion tracking and statistics.
+//
+// Algorithm 1 split between host and device: the host adds arriving kernels
+// to R (kl_submit) and evaluates the performance model once per set of kernel
+// types (the paper re-uses a kernel's earlier slice size when it was submitted
+// before; here the CP / balanced-split table per type pair is cached the same
+// way); FindCoSchedule and the "repeat the co-schedule until a kernel runs out"
+// loop run on the device (kl_cosched.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "kernelet.h"
+#include "kl_internal.h"
+#include "tenants.cuh"
+
+namespace kl {
+int cosched_occupancy(int* ctas_per_sm);
+int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, cudaStream_t stream);
+int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s);
+namespace model {
+int pair(const kl_model_params& g, const kl_profile& pa, const kl_profile& pb, uint32_t slots, int states,
+         uint32_t policy, uint32_t fixed_a, double* cA, double* cB, double* cpv, double* dT, double* solo,
+         uint32_t* best_a);
+bool pruned(double pur_a, double mur_a, double pur_b, double mur_b, double ap, double am);
+}  // namespace model
+}  // namespace kl
+
+using namespace kl;
+
+namespace {
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+size_t args_size_of(uint32_t type) {
+  switch (type) {
+    case KL_T_GATHER: return sizeof(kl_args_gather);
+    case KL_T_BLACKSCHOLES: return sizeof(kl_args_blackscholes);
+    case KL_T_GEMM_F32: return sizeof(kl_args_gemm_f32);
+    case KL_T_SPMV_CSR: return sizeof(kl_args_spmv_csr);
+    case KL_T_PCHASE: return sizeof(kl_args_pchase);
+    case KL_T_TRIAD: return sizeof(kl_args_triad);
+    case KL_T_HIST256: return sizeof(kl_args_hist256);
+    case KL_T_ESCAPE: return sizeof(kl_args_escape);
+    case KL_T_BITONIC: return sizeof(kl_args_bitonic);
+    case KL_T_MATADD: return sizeof(kl_args_matadd);
+    default: return 0;
+  }
+}
+
+bool a16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Argument checks a plain launch of the tenant would need to be safe.
+int validate_args(uint32_t type, const void* a) {
+  switch (type) {
+    case KL_T_GATHER: {
+      const kl_args_gather* g = (const kl_args_gather*)a;
+      if (!g->a || !g->idx || !g->out || g->n == 0 || !a16(g->idx) || !a16(g->out)) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_BLACKSCHOLES: {
+      const kl_args_blackscholes* b = (const kl_args_blackscholes*)a;
+      if (!b->S || !b->K || !b->r || !b->v || !b->T || !b->call || !b->put || b->n == 0) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_GEMM_F32: {
+      const kl_args_gemm_f32* g = (const kl_args_gemm_f32*)a;
+      if (!g->A || !g->B || !g->C || g->M == 0 || g->N == 0 || g->K == 0) return KL_EINVAL;
+      if (g->N % 4 || g->K % 4 || !a16(g->A) || !a16(g->B) || !a16(g->C)) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_SPMV_CSR: {
+      const kl_args_spmv_csr* s = (const kl_args_spmv_csr*)a;
+      if (!s->rowptr || !s->col || !s->val || !s->x || !s->y || s->nrows == 0 || s->ncols == 0) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_PCHASE: {
+      const kl_args_pchase* p = (const kl_args_pchase*)a;
+      if (!p->next || !p->start || !p->end || p->N == 0 || p->nchasers == 0) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_TRIAD: {
+      const kl_args_triad* t = (const kl_args_triad*)a;
+      if (!t->a || !t->b || !t->c || t->n == 0 || !a16(t->a) || !a16(t->b) || !a16(t->c)) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_HIST256: {
+      const kl_args_hist256* h = (const kl_args_hist256*)a;
+      if (!h->data || !h->hist || h->n == 0 || !a16(h->data)) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_ESCAPE: {
+      const kl_args_escape* e = (const kl_args_escape*)a;
+      if (!e->count || e->width == 0 || e->height == 0) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_BITONIC: {
+      const kl_args_bitonic* b = (const kl_args_bitonic*)a;
+      if (!b->in || !b->out || b->log2n < 1 || b->log2n > 30) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_MATADD: {
+      const kl_args_matadd* m = (const kl_args_matadd*)a;
+      if (!m->a || !m->b || !m->c || m->n == 0 || m->n % 16) return KL_EINVAL;
+      return KL_OK;
+    }
+    default: return KL_EINVAL;
+  }
+}
+
+// Pull granularity per type (blocks per slice) when the descriptor leaves it to
+// the runtime; chosen so one atomic covers roughly 16-64 KB of traffic or one
+// long block.
+uint32_t default_slice(uint32_t type) {
+  switch (type) {
+    case KL_T_GATHER: return 4;
+    case KL_T_BLACKSCHOLES: return 8;
+    case KL_T_GEMM_F32: return 1;
+    case KL_T_SPMV_CSR: return 8;
+    case KL_T_PCHASE: return 1;
+    case KL_T_TRIAD: return 2;
+    case KL_T_HIST256: return 2;
+    case KL_T_ESCAPE: return 8;
+    case KL_T_BITONIC: return 1;
+    case KL_T_MATADD: return 8;
+    default: return 1;
+  }
+}
+
+// Built-in model inputs used until measured profiles are loaded: rough
+// instruction mixes by construction of each tenant body (flagged as such by
+// kl_profile.valid = 2).
+kl_profile builtin_profile(uint32_t type) {
+  kl_profile p{};
+  p.m_c = 4.0;
+  p.m_u = 32.0;
+  p.warps_per_block = 8;
+  p.valid = 2;
+  switch (type) {
+    case KL_T_GATHER: p.R_m = 0.30; p.f_u = 0.8; p.L0 = 900; p.I_block = 8 * 40; p.PUR = 0.05; p.MUR = 0.50; break;
+    case KL_T_BLACKSCHOLES: p.R_m = 0.03; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 300; p.PUR = 0.60; p.MUR = 0.30; break;
+    case KL_T_GEMM_F32: p.R_m = 0.01; p.f_u = 0.0; p.L0 = 700; p.I_block = 8 * 40000; p.PUR = 0.80; p.MUR = 0.05; break;
+    case KL_T_SPMV_CSR: p.R_m = 0.25; p.f_u = 0.5; p.L0 = 900; p.I_block = 8 * 120; p.PUR = 0.15; p.MUR = 0.60; break;
+    case KL_T_PCHASE: p.R_m = 0.30; p.f_u = 1.0; p.L0 = 1000; p.I_block = 8 * 1000; p.PUR = 0.01; p.MUR = 0.10; break;
+    case KL_T_TRIAD: p.R_m = 0.20; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 60; p.PUR = 0.05; p.MUR = 0.90; break;
+    case KL_T_HIST256: p.R_m = 0.05; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 600; p.PUR = 0.40; p.MUR = 0.40; break;
+    case KL_T_ESCAPE: p.R_m = 0.001; p.f_u = 0.0; p.L0 = 700; p.I_block = 8 * 1500; p.PUR = 0.70; p.MUR = 0.01; break;
+    case KL_T_BITONIC: p.R_m = 0.10; p.f_u = 0.0; p.L0 = 500; p.I_block = 8 * 400; p.PUR = 0.30; p.MUR = 0.30; break;
+    case KL_T_MATADD: p.R_m = 0.25; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 12; p.PUR = 0.05; p.MUR = 0.70; break;
+    default: p.valid = 0; break;
+  }
+  return p;
+}
+
+struct Pending {
+  TenantDev td;
+  uint64_t footprint;
+  uint64_t t_submit;
+  kl_handle handle;
+};
+
+struct Record {
+  kl_tenant_stats st{};
+  kl_handle handle = 0;
+};
+
+enum RunKind { kNone = 0, kCosched = 1, kBaseline = 2 };
+
+}  // namespace
+
+struct kl_runtime {
+  std::mutex mu;
+  kl_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint32_t n_sm = 0, slots = 0, occupancy = 0;
+  uint32_t cap = 0, cap_phases = 0;
+  TenantDev* d_tenants = nullptr;
+  RunDev* d_run = nullptr;
+  PhaseDev* d_phases = nullptr;
+  TenantDev* h_tenants = nullptr;
+  RunDev* h_run = nullptr;
+  PhaseDev* h_phases = nullptr;
+  std::vector<Pending> pending;
+  uint64_t pending_footprint = 0;
+  uint64_t run_id = 1;       // id of the run the pending set will become
+  // in-flight / last run
+  int kind = kNone;
+  bool in_flight = false;
+  uint64_t flight_id = 0;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  std::vector<Pending> flight;      // tenants of the in-flight run
+  std::vector<cudaEvent_t> tenant_ev;  // baseline per-tenant completion events
+  std::map<uint64_t, std::vector<Record>> history;  // retired runs (last few)
+  kl_run_stats last{};
+  std::vector<kl_phase> last_phases;
+  // model
+  kl_model_params mp{};
+  kl_profile prof[KL_T_COUNT];
+  bool table_valid = false;
+  double cp[KL_T_COUNT][KL_T_COUNT];
+  uint32_t slots_a[KL_T_COUNT][KL_T_COUNT];
+  uint32_t allowed[KL_T_COUNT][KL_T_COUNT];
+  uint32_t table_types = 0;  // bit mask of types in the cached table
+  // baselines
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_join;
+  cudaEvent_t ev_fork = nullptr;
+};
+
+namespace {
+
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? KL_OK : KL_ECUDA; }
+
+kl_handle make_handle(uint64_t run, uint32_t idx) { return (run << 24) | (uint64_t)(idx + 1); }
+void split_handle(kl_handle h, uint64_t* run, uint32_t* idx) {
+  *run = h >> 24;
+  *idx = (uint32_t)(h & 0xffffffu) - 1;
+}
+
+// CP table for every pair of types in `mask` (Section 4.4 model + Section 4.3
+// pruning). Cached until profiles, parameters or the type set change.
+int ensure_table(kl_runtime* rt, uint32_t mask) {
+  if (rt->table_valid && (rt->table_types & mask) == mask) return KL_OK;
+  const uint32_t want = mask | (rt->table_valid ? rt->table_types : 0u);
+  const uint32_t S = rt->slots;
+  std::vector<double> a(S), b(S), c(S), d(S);
+  for (uint32_t i = 0; i < KL_T_COUNT; ++i)
+    for (uint32_t j = 0; j < KL_T_COUNT; ++j) {
+      rt->cp[i][j] = 0.0;
+      rt->slots_a[i][j] = S / 2 ? S / 2 : 1;
+      rt->allowed[i][j] = 1;
+    }
+  if (S >= 2) {
+    for (uint32_t i = 0; i < KL_T_COUNT; ++i) {
+      if (!(want & (1u << i))) continue;
+      for (uint32_t j = 0; j < KL_T_COUNT; ++j) {
+        if (!(want & (1u << j))) continue;
+        double solo[2];
+        uint32_t best = 1;
+        int rc = model::pair(rt->mp, rt->prof[i], rt->prof[j], S, (int)rt->cfg.model_states, rt->cfg.ratio_policy,
+                             rt->cfg.fixed_slots_a, a.data(), b.data(), c.data(), d.data(), solo, &best);
+        if (rc) return rc;
+        rt->cp[i][j] = c[best - 1];
+        rt->slots_a[i][j] = best;
+        rt->allowed[i][j] = model::pruned(rt->prof[i].PUR, rt->prof[i].MUR, rt->prof[j].PUR, rt->prof[j].MUR,
+                                          rt->cfg.alpha_p, rt->cfg.alpha_m)
+                                ? 0u
+                                : 1u;
+      }
+    }
+  }
+  rt->table_types = want;
+  rt->table_valid = true;
+  return KL_OK;
+}
+
+void record_history(kl_runtime* rt, uint64_t id, std::vector<Record>&& recs) {
+  rt->history[id] = std::move(recs);
+  while (rt->history.size() > 8) rt->history.erase(rt->history.begin());
+}
+
+// Move a finished run into the history. Caller holds the lock and has seen
+// ev_done complete.
+int retire(kl_runtime* rt) {
+  if (!rt->in_flight) return KL_OK;
+  const uint32_t n = (uint32_t)rt->flight.size();
+  std::vector<Record> recs(n);
+  int run_err = KL_OK;
+  if (rt->kind == kCosched) {
+    const RunDev& R = *rt->h_run;
+    run_err = R.error;
+    uint32_t np = std::min(R.phase_seq + 1, rt->cap_phases);
+    rt->last_phases.clear();
+    for (uint32_t k = 0; k < np; ++k) {
+      const PhaseDev& p = rt->h_phases[k];
+      kl_phase q{};
+      q.A = p.A;
+      q.B = p.B;
+      q.slots_a = p.slots_a;
+      q.slots_b = p.slots_b;
+      q.cp = p.cp;
+      q.t_ns = p.t;
+      q.trigger = p.trigger;
+      q.n_pending = p.n_pending;
+      q.pending_mask = p.pending;
+      rt->last_phases.push_back(q);
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+      const TenantDev& t = rt->h_tenants[i];
+      Record& r = recs[i];
+      r.handle = rt->flight[i].handle;
+      r.st.t_submit_ns = rt->flight[i].t_submit;
+      r.st.t_start_ns = t.t_start;
+      r.st.t_end_ns = t.t_end;
+      r.st.t_launch_ns = R.t_launch;
+      r.st.slices = t.slices;
+      r.st.blocks = t.done;
+      if (t.done == t.total && t.status == KL_DONE) {
+        r.st.state = KL_DONE;
+      } else {
+        r.st.state = KL_ERROR;
+        r.st.error = run_err ? run_err : KL_ESTATE;
+      }
+    }
+    rt->last.n_tenants = n;
+    rt->last.n_phases = np;
+    rt->last.error = run_err;
+    rt->last.slots_per_sm = rt->slots;
+    rt->last.grid_ctas = rt->slots * rt->n_sm;
+    rt->last.t_launch_ns = R.t_launch;
+    rt->last.t_end_ns = R.t_end;
+  } else {
+    // baseline: per-tenant completion from events relative to the fork
+    for (uint32_t i = 0; i < n; ++i) {
+      Record& r = recs[i];
+      r.handle = rt->flight[i].handle;
+      r.st.state = KL_DONE;
+      r.st.t_submit_ns = rt->flight[i].t_submit;
+      float ms = 0.f;
+      if (i < rt->tenant_ev.size() && cudaEventElapsedTime(&ms, rt->ev_start, rt->tenant_ev[i]) == cudaSuccess)
+        r.st.t_end_ns = (uint64_t)((double)ms * 1e6);
+      r.st.blocks = (uint32_t)tn::total_blocks(rt->flight[i].td.type, rt->flight[i].td.args);
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, rt->ev_start, rt->ev_done);
+    rt->last = kl_run_stats{};
+    rt->last.n_tenants = n;
+    rt->last.t_launch_ns = 0;
+    rt->last.t_end_ns = (uint64_t)((double)ms * 1e6);
+    rt->last_phases.clear();
+  }
+  record_history(rt, rt->flight_id, std::move(recs));
+  rt->flight.clear();
+  rt->in_flight = false;
+  rt->kind = kNone;
+  return run_err;
+}
+
+// Non-blocking check of the in-flight run.
+int progress(kl_runtime* rt) {
+  if (!rt->in_flight) return KL_OK;
+  cudaError_t e = cudaEventQuery(rt->ev_done);
+  if (e == cudaErrorNotReady) return KL_EAGAIN;
+  if (e != cudaSuccess) return KL_ECUDA;
+  retire(rt);
+  return KL_OK;
+}
+
+int wait_flight(kl_runtime* rt, std::unique_lock<std::mutex>& lk, uint64_t timeout_ns) {
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    int rc = progress(rt);
+    if (rc != KL_EAGAIN) return rc;
+    if (now_ns() - t0 >= timeout_ns) return KL_ETIMEDOUT;
+    lk.unlock();
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+    lk.lock();
+  }
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" int kl_abi_version(void) { return KL_ABI_VERSION; }
+
+extern "C" const char* kl_strerror(int code) {
+  switch (code) {
+    case KL_OK: return "ok";
+    case KL_EINVAL: return "invalid argument";
+    case KL_ENOMEM: return "out of memory";
+    case KL_EAGAIN: return "try again (queue full, over the memory cap, or a run in flight)";
+    case KL_ETIMEDOUT: return "host wait timed out";
+    case KL_ECUDA: return "CUDA runtime error";
+    case KL_EDEVICE_TIMEOUT: return "device-side wait exceeded its limit";
+    case KL_ESTATE: return "invalid state";
+    case KL_ENOTFOUND: return "unknown handle";
+    case KL_EOVERFLOW: return "device table overflow";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int kl_config_default(kl_config* c) {
+  if (!c) return KL_EINVAL;
+  memset(c, 0, sizeof(*c));
+  c->device = 0;
+  c->slots_per_sm = 0;
+  c->max_tenants = 4096;
+  c->model_states = 3;
+  c->ratio_policy = KL_RATIO_BALANCED;
+  c->fixed_slots_a = 2;
+  c->device_wait_limit_ns = 2000000000ull;
+  c->mem_cap_bytes = 0;
+  c->alpha_p = -1.0;
+  c->alpha_m = -1.0;
+  return KL_OK;
+}
+
+extern "C" int kl_tenant_shape_of(uint32_t type, const void* args, uint32_t args_size, kl_tenant_shape* out) {
+  if (!out || !args || type >= KL_T_COUNT || args_size != args_size_of(type)) return KL_EINVAL;
+  int rc = validate_args(type, args);
+  if (rc) return rc;
+  unsigned char blob[KL_MAX_ARGS_BYTES] = {0};
+  memcpy(blob, args, args_size);
+  memset(out, 0, sizeof(*out));
+  out->grid[0] = tn::stage_blocks(type, blob, 0);
+  out->grid[1] = out->grid[2] = 1;
+  out->block[0] = KL_BLOCK_THREADS;
+  out->block[1] = out->block[2] = 1;
+  out->nstages = tn::nstages(type, blob);
+  out->smem_bytes = tn::smem_bytes(type);
+  out->total_blocks = tn::total_blocks(type, blob);
+  return KL_OK;
+}
+
+extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime** out) {
+  if (!out) return KL_EINVAL;
+  *out = nullptr;
+  kl_config cfg;
+  if (cfg_in)
+    cfg = *cfg_in;
+  else
+    kl_config_default(&cfg);
+  if (cfg.model_states != 2 && cfg.model_states != 3) return KL_EINVAL;
+  if (cfg.max_tenants == 0 || cfg.max_tenants > (1u << 20)) return KL_EINVAL;
+  if (cfg.slots_per_sm > KL_MAX_SLOTS || cfg.ratio_policy > 2) return KL_EINVAL;
+  if (cfg.device_wait_limit_ns == 0) cfg.device_wait_limit_ns = 2000000000ull;
+  if (cudaSetDevice(cfg.device) != cudaSuccess) return KL_ECUDA;
+  kl_runtime* rt = new (std::nothrow) kl_runtime();
+  if (!rt) return KL_ENOMEM;
+  rt->cfg = cfg;
+  rt->device = cfg.device;
+  rt->stream = (cudaStream_t)cuda_stream;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, cfg.device) != cudaSuccess) goto fail_cuda;
+  rt->n_sm = (uint32_t)std::min(v, kMaxSM);
+  {
+    int occ = 0;
+    if (cosched_occupancy(&occ) != 0 || occ < 1) goto fail_cuda;
+    rt->occupancy = (uint32_t)occ;
+    uint32_t s = cfg.slots_per_sm ? cfg.slots_per_sm : (uint32_t)occ;
+    s = std::min<uint32_t>(std::min<uint32_t>(s, (uint32_t)occ), KL_MAX_SLOTS);
+    rt->slots = s;
+  }
+  rt->cap = cfg.max_tenants;
+  rt->cap_phases = 4 * rt->cap + 16;
+  if (cudaMalloc(&rt->d_tenants, sizeof(TenantDev) * rt->cap) != cudaSuccess) goto fail_mem;
+  if (cudaMalloc(&rt->d_run, sizeof(RunDev)) != cudaSuccess) goto fail_mem;
+  if (cudaMalloc(&rt->d_phases, sizeof(PhaseDev) * rt->cap_phases) != cudaSuccess) goto fail_mem;
+  if (cudaMallocHost(&rt->h_tenants, sizeof(TenantDev) * rt->cap) != cudaSuccess) goto fail_mem;
+  if (cudaMallocHost(&rt->h_run, sizeof(RunDev)) != cudaSuccess) goto fail_mem;
+  if (cudaMallocHost(&rt->h_phases, sizeof(PhaseDev) * rt->cap_phases) != cudaSuccess) goto fail_mem;
+  if (cudaEventCreate(&rt->ev_start) != cudaSuccess || cudaEventCreate(&rt->ev_done) != cudaSuccess ||
+      cudaEventCreateWithFlags(&rt->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    goto fail_cuda;
+  // model defaults: device properties, built-in profiles
+  {
+    rt->mp.n_sm = rt->n_sm;
+    rt->mp.n_sched = 4;
+    int khz = 0;
+    rt->mp.f_sm_hz = (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, cfg.device) == cudaSuccess && khz > 0)
+                         ? khz * 1e3
+                         : 1.9e9;
+    rt->mp.dram_bytes_per_s = 6.75e12;
+    rt->mp.sector_bytes = 32.0;
+    rt->mp.a0 = 1.0;
+    rt->mp.b0 = 0.0;
+    for (uint32_t t = 0; t < KL_T_COUNT; ++t) rt->prof[t] = builtin_profile(t);
+  }
+  *out = rt;
+  return KL_OK;
+fail_mem:
+  kl_destroy(rt);
+  return KL_ENOMEM;
+fail_cuda:
+  kl_destroy(rt);
+  return KL_ECUDA;
+}
+
+extern "C" int kl_destroy(kl_runtime* rt) {
+  if (!rt) return KL_EINVAL;
+  int rc = KL_OK;
+  {
+    std::unique_lock<std::mutex> lk(rt->mu);
+    if (rt->in_flight) {
+      int w = wait_flight(rt, lk, rt->cfg.device_wait_limit_ns * 4 + 1000000000ull);
+      if (w == KL_ETIMEDOUT) rc = KL_ESTATE;
+    }
+  }
+  if (rc == KL_ESTATE) return rc;  // leave resources: the GPU may still use them
+  cudaFree(rt->d_tenants);
+  cudaFree(rt->d_run);
+  cudaFree(rt->d_phases);
+  cudaFreeHost(rt->h_tenants);
+  cudaFreeHost(rt->h_run);
+  cudaFreeHost(rt->h_phases);
+  if (rt->ev_start) cudaEventDestroy(rt->ev_start);
+  if (rt->ev_done) cudaEventDestroy(rt->ev_done);
+  if (rt->ev_fork) cudaEventDestroy(rt->ev_fork);
+  for (cudaEvent_t e : rt->tenant_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : rt->side_join) cudaEventDestroy(e);
+  for (cudaStream_t s : rt->side) cudaStreamDestroy(s);
+  delete rt;
+  return KL_OK;
+}
+
+extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out) {
+  if (!rt || !d || !out) return KL_EINVAL;
+  *out = 0;
+  if (d->type >= KL_T_COUNT || !d->args || d->args_size != args_size_of(d->type)) return KL_EINVAL;
+  if (d->block[0] != KL_BLOCK_THREADS || d->block[1] != 1 || d->block[2] != 1) return KL_EINVAL;
+  kl_tenant_shape sh;
+  int rc = kl_tenant_shape_of(d->type, d->args, d->args_size, &sh);
+  if (rc) return rc;
+  if (d->grid[0] != sh.grid[0] || d->grid[1] != 1 || d->grid[2] != 1) return KL_EINVAL;
+  if (d->smem_bytes != 0 && d->smem_bytes < sh.smem_bytes) return KL_EINVAL;
+  if (sh.total_blocks == 0 || sh.total_blocks >= (1ull << 31)) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  if (rt->pending.size() >= rt->cap) return KL_EAGAIN;
+  if (rt->cfg.mem_cap_bytes && rt->pending_footprint + d->footprint_bytes > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
+  Pending p;
+  memset(&p.td, 0, sizeof(p.td));
+  p.td.type = d->type;
+  p.td.slice = d->slice_blocks ? d->slice_blocks : default_slice(d->type);
+  p.td.total = (uint32_t)sh.total_blocks;
+  p.td.nstages = sh.nstages;
+  p.td.index = (uint32_t)rt->pending.size();
+  memcpy(p.td.args, d->args, d->args_size);
+  p.footprint = d->footprint_bytes;
+  p.t_submit = now_ns();
+  p.handle = make_handle(rt->run_id, p.td.index);
+  rt->pending.push_back(p);
+  rt->pending_footprint += d->footprint_bytes;
+  *out = p.handle;
+  return KL_OK;
+}
+
+// Plan and start the pending set; caller holds rt->mu.
+static int launch_locked(kl_runtime* rt) {
+  if (rt->in_flight && progress(rt) == KL_EAGAIN) return KL_EAGAIN;
+  const uint32_t n = (uint32_t)rt->pending.size();
+  if (n == 0) return KL_OK;
+  if (cudaSetDevice(rt->device) != cudaSuccess) return KL_ECUDA;
+  uint32_t mask = 0;
+  for (const Pending& p : rt->pending) mask |= 1u << p.td.type;
+  int rc = ensure_table(rt, mask);
+  if (rc) return rc;
+  // device image: run state, tenants, the "plan first" phase
+  RunDev& R = *rt->h_run;
+  memset(&R, 0, sizeof(R));
+  R.n_tenants = n;
+  R.slots = rt->slots;
+  R.max_phases = std::min(rt->cap_phases, 4 * n + 16);
+  R.n_types = KL_T_COUNT;
+  R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
+  memcpy(R.cp, rt->cp, sizeof(R.cp));
+  memcpy(R.slots_a, rt->slots_a, sizeof(R.slots_a));
+  memcpy(R.allowed, rt->allowed, sizeof(R.allowed));
+  for (uint32_t i = 0; i < n; ++i) rt->h_tenants[i] = rt->pending[i].td;
+  PhaseDev first{};
+  first.A = -2;
+  first.B = -1;
+  rt->h_phases[0] = first;
+  cudaStream_t s = rt->stream;
+  rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
+  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_tenants, rt->h_tenants, sizeof(TenantDev) * n, cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_phases, rt->h_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
+  if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, rt->slots, s) != 0) rc = KL_ECUDA;
+  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_tenants, rt->d_tenants, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
+  if (!rc)
+    rc = cuda_ok(cudaMemcpyAsync(rt->h_phases, rt->d_phases, sizeof(PhaseDev) * R.max_phases, cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_done, s));
+  if (rc) return rc;
+  rt->flight.swap(rt->pending);
+  rt->pending.clear();
+  rt->pending_footprint = 0;
+  rt->in_flight = true;
+  rt->kind = kCosched;
+  rt->flight_id = rt->run_id++;
+  return KL_OK;
+}
+
+extern "C" int kl_launch(kl_runtime* rt) {
+  if (!rt) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  return launch_locked(rt);
+}
+
+extern "C" int kl_launch_baseline(kl_runtime* rt, int mode, uint32_t nstreams) {
+  if (!rt || (mode != KL_BASE_SERIAL && mode != KL_BASE_MULTISTREAM)) return KL_EINVAL;
+  if (mode == KL_BASE_MULTISTREAM && (nstreams == 0 || nstreams > 256)) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  if (rt->in_flight && progress(rt) == KL_EAGAIN) return KL_EAGAIN;
+  const uint32_t n = (uint32_t)rt->pending.size();
+  if (n == 0) return KL_OK;
+  if (cudaSetDevice(rt->device) != cudaSuccess) return KL_ECUDA;
+  while (rt->tenant_ev.size() < n) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return KL_ECUDA;
+    rt->tenant_ev.push_back(e);
+  }
+  if (mode == KL_BASE_MULTISTREAM) {
+    while (rt->side.size() < nstreams) {
+      cudaStream_t s;
+      cudaEvent_t e;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return KL_ECUDA;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return KL_ECUDA;
+      rt->side.push_back(s);
+      rt->side_join.push_back(e);
+    }
+  }
+  cudaStream_t s = rt->stream;
+  int rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
+  if (mode == KL_BASE_SERIAL) {
+    for (uint32_t i = 0; i < n && !rc; ++i) {
+      if (native_launch_tenant(rt->pending[i].td.type, rt->pending[i].td.args, s) != 0) rc = KL_ECUDA;
+      if (!rc) rc = cuda_ok(cudaEventRecord(rt->tenant_ev[i], s));
+    }
+  } else {
+    rc = rc ? rc : cuda_ok(cudaEventRecord(rt->ev_fork, s));
+    for (uint32_t k = 0; k < nstreams && !rc; ++k) rc = cuda_ok(cudaStreamWaitEvent(rt->side[k], rt->ev_fork, 0));
+    for (uint32_t i = 0; i < n && !rc; ++i) {
+      cudaStream_t si = rt->side[i % nstreams];
+      if (native_launch_tenant(rt->pending[i].td.type, rt->pending[i].td.args, si) != 0) rc = KL_ECUDA;
+      if (!rc) rc = cuda_ok(cudaEventRecord(rt->tenant_ev[i], si));
+    }
+    for (uint32_t k = 0; k < nstreams && !rc; ++k) {
+      rc = cuda_ok(cudaEventRecord(rt->side_join[k], rt->side[k]));
+      if (!rc) rc = cuda_ok(cudaStreamWaitEvent(s, rt->side_join[k], 0));
+    }
+  }
+  if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_done, s));
+  if (rc) return rc;
+  rt->flight.swap(rt->pending);
+  rt->pending.clear();
+  rt->pending_footprint = 0;
+  rt->in_flight = true;
+  rt->kind = kBaseline;
+  rt->flight_id = rt->run_id++;
+  return KL_OK;
+}
+
+static int lookup(kl_runtime* rt, kl_handle h, kl_tenant_stats* st) {
+  uint64_t run;
+  uint32_t idx;
+  split_handle(h, &run, &idx);
+  if (h == 0) return KL_ENOTFOUND;
+  if (run == rt->run_id) {
+    if (idx >= rt->pending.size() || rt->pending[idx].handle != h) return KL_ENOTFOUND;
+    memset(st, 0, sizeof(*st));
+    st->state = KL_PENDING;
+    st->t_submit_ns = rt->pending[idx].t_submit;
+    return KL_OK;
+  }
+  if (rt->in_flight && run == rt->flight_id) {
+    if (idx >= rt->flight.size()) return KL_ENOTFOUND;
+    memset(st, 0, sizeof(*st));
+    st->state = KL_RUNNING;
+    st->t_submit_ns = rt->flight[idx].t_submit;
+    return KL_OK;
+  }
+  auto it = rt->history.find(run);
+  if (it == rt->history.end() || idx >= it->second.size()) return KL_ENOTFOUND;
+  *st = it->second[idx].st;
+  return KL_OK;
+}
+
+extern "C" int kl_poll(kl_runtime* rt, kl_handle h, int* state) {
+  if (!rt || !state) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  int p = progress(rt);
+  if (p != KL_OK && p != KL_EAGAIN) return p;
+  kl_tenant_stats st;
+  int rc = lookup(rt, h, &st);
+  if (rc) return rc;
+  *state = st.state;
+  return KL_OK;
+}
+
+extern "C" int kl_wait(kl_runtime* rt, kl_handle h, uint64_t timeout_ns) {
+  if (!rt) return KL_EINVAL;
+  std::unique_lock<std::mutex> lk(rt->mu);
+  kl_tenant_stats st;
+  int rc = lookup(rt, h, &st);
+  if (rc) return rc;
+  if (st.state == KL_PENDING) return KL_ESTATE;  // not launched: waiting would never end
+  if (st.state == KL_RUNNING) {
+    rc = wait_flight(rt, lk, timeout_ns);
+    if (rc == KL_ETIMEDOUT || rc == KL_ECUDA) return rc;
+    rc = lookup(rt, h, &st);
+    if (rc) return rc;
+  }
+  return st.state == KL_DONE ? KL_OK : (st.error ? st.error : KL_ESTATE);
+}
+
+extern "C" int kl_drain(kl_runtime* rt, uint64_t timeout_ns) {
+  if (!rt) return KL_EINVAL;
+  std::unique_lock<std::mutex> lk(rt->mu);
+  int rc;
+  if (rt->in_flight) {
+    rc = wait_flight(rt, lk, timeout_ns);
+    if (rc == KL_ETIMEDOUT || rc == KL_ECUDA) return rc;
+  }
+  if (!rt->pending.empty()) {
+    rc = launch_locked(rt);
+    if (rc) return rc;
+  }
+  if (rt->in_flight) {
+    rc = wait_flight(rt, lk, timeout_ns);
+    if (rc == KL_ETIMEDOUT || rc == KL_ECUDA) return rc;
+  }
+  return rt->last.error;
+}
+
+extern "C" int kl_get_stats(kl_runtime* rt, kl_handle h, kl_tenant_stats* out) {
+  if (!rt || !out) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  progress(rt);
+  return lookup(rt, h, out);
+}
+
+extern "C" int kl_get_run_stats(kl_runtime* rt, kl_run_stats* out) {
+  if (!rt || !out) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  progress(rt);
+  *out = rt->last;
+  out->slots_per_sm = rt->slots;
+  out->grid_ctas = rt->slots * rt->n_sm;
+  return KL_OK;
+}
+
+extern "C" int kl_get_phases(kl_runtime* rt, kl_phase* out, uint32_t cap, uint32_t* n) {
+  if (!rt || !n || (cap && !out)) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  progress(rt);
+  *n = (uint32_t)rt->last_phases.size();
+  for (uint32_t i = 0; i < cap && i < *n; ++i) out[i] = rt->last_phases[i];
+  return KL_OK;
+}
+
+extern "C" int kl_set_profiles(kl_runtime* rt, const kl_profile* p, uint32_t n) {
+  if (!rt || !p || n > KL_T_COUNT) return KL_EINVAL;
+  for (uint32_t t = 0; t < n; ++t)
+    if (p[t].valid && (!(p[t].R_m >= 0.0 && p[t].R_m <= 1.0) || !(p[t].f_u >= 0.0 && p[t].f_u <= 1.0) ||
+                       !(p[t].L0 >= 0.0) || !(p[t].I_block > 0.0) || p[t].warps_per_block == 0))
+      return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  for (uint32_t t = 0; t < n; ++t)
+    if (p[t].valid) rt->prof[t] = p[t];
+  rt->table_valid = false;
+  return KL_OK;
+}
+
+extern "C" int kl_set_model_params(kl_runtime* rt, const kl_model_params* mp) {
+  if (!rt || !mp || mp->n_sm == 0 || mp->n_sched == 0 || !(mp->f_sm_hz > 0) || !(mp->dram_bytes_per_s > 0) ||
+      !(mp->sector_bytes > 0))
+    return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  rt->mp = *mp;
+  rt->table_valid = false;
+  return KL_OK;
+}
+
+extern "C" int kl_get_model_params(kl_runtime* rt, kl_model_params* out) {
+  if (!rt || !out) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  *out = rt->mp;
+  return KL_OK;
+}
+
+extern "C" int kl_get_cp_table(kl_runtime* rt, double* cp, uint32_t* slots_a, uint8_t* allowed) {
+  if (!rt) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  int rc = ensure_table(rt, (1u << KL_T_COUNT) - 1);
+  if (rc) return rc;
+  for (uint32_t i = 0; i < KL_T_COUNT; ++i)
+    for (uint32_t j = 0; j < KL_T_COUNT; ++j) {
+      if (cp) cp[i * KL_T_COUNT + j] = rt->cp[i][j];
+      if (slots_a) slots_a[i * KL_T_COUNT + j] = rt->slots_a[i][j];
+      if (allowed) allowed[i * KL_T_COUNT + j] = (uint8_t)rt->allowed[i][j];
+    }
+  return KL_OK;
+}

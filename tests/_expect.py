@@ -1,0 +1,76 @@
+"""Expected tenant outputs from the CPU oracle, and the comparisons the parity
+tests use (bit-exact except the SpMV reduction, whose tolerance is derived
+from its summation depth)."""
+import math
+
+import numpy as np
+
+from oracle import tenants as OT
+
+U = 2.0 ** -24    # unit roundoff of binary32
+
+
+def expected(name: str, inp: dict) -> dict:
+    if name == "gather":
+        return {"out": OT.gather(inp["a"], inp["idx"])}
+    if name == "blackscholes":
+        c, p = OT.blackscholes(inp["S"], inp["K"], inp["r"], inp["v"], inp["T"])
+        return {"call": c, "put": p}
+    if name == "gemm_f32":
+        return {"C": OT.gemm_f32(inp["A"], inp["B"])}
+    if name == "spmv_csr":
+        y32, y64, asum = OT.spmv_csr(inp["rowptr"], inp["col"], inp["val"], inp["x"])
+        return {"y": y32, "_y64": y64, "_asum": asum}
+    if name == "pchase":
+        return {"end": OT.pchase(inp["next"], inp["start"], inp["hops"])}
+    if name == "triad":
+        return {"a": OT.triad(inp["b"], inp["c"], inp["s"])}
+    if name == "hist256":
+        return {"hist": OT.hist256(inp["data"])}
+    if name == "escape":
+        return {"count": OT.escape(inp["width"], inp["height"], inp["max_iter"], inp["x0"], inp["y0"],
+                                   inp["dx"], inp["dy"])}
+    if name == "bitonic":
+        return {"out": OT.sort_u32(inp["data"])}
+    if name == "matadd":
+        return {"c": OT.matadd(inp["a"], inp["b"])}
+    raise ValueError(name)
+
+
+def spmv_bound(rowptr, asum):
+    """|y_gpu - y_exact| <= (ceil(len/8) + 3 + 1) u sum|a x| per row: each of the
+    8 lanes runs a fused chain over ceil(len/8) terms, then 3 butterfly adds."""
+    deg = np.diff(rowptr.astype(np.int64))
+    depth = np.ceil(deg / 8.0) + 4.0
+    return depth * U * asum
+
+
+def same_bits(a, b) -> bool:
+    a = np.ascontiguousarray(a)
+    b = np.ascontiguousarray(b)
+    if a.shape != b.shape:
+        return False
+    if a.dtype.kind == "f":
+        return np.array_equal(a.view(np.uint32 if a.itemsize == 4 else np.uint64),
+                              b.astype(a.dtype).view(np.uint32 if a.itemsize == 4 else np.uint64))
+    return np.array_equal(a, b.astype(a.dtype) if a.dtype != b.dtype else b)
+
+
+def check(name: str, inp: dict, got: dict, exp: dict):
+    """Raises AssertionError with a short reason when `got` misses the bar."""
+    if name == "spmv_csr":
+        y = got["y"].astype(np.float64)
+        bound = spmv_bound(inp["rowptr"], exp["_asum"])
+        err = np.abs(y - exp["_y64"])
+        bad = np.nonzero(err > bound)[0]
+        assert len(bad) == 0, f"spmv rows over bound: {bad[:5]} err {err[bad[:5]]} bound {bound[bad[:5]]}"
+        return
+    for k, v in exp.items():
+        g = got[k].reshape(v.shape) if got[k].size == v.size else got[k]
+        if not same_bits(g, v):
+            gg = np.asarray(g).ravel()
+            vv = np.asarray(v).ravel()
+            diff = np.nonzero(gg != vv)[0] if gg.shape == vv.shape else []
+            raise AssertionError(f"{name}.{k}: {len(diff)} elements differ, first {list(diff[:5])}: "
+                                 f"got {gg[diff[:3]] if len(diff) else gg.shape} want "
+                                 f"{vv[diff[:3]] if len(diff) else vv.shape}")

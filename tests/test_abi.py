@@ -1,0 +1,156 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry
+point, rejects bad input without a GPU, and its pure host functions (Markov
+model, pair evaluation, greedy plan, pruning) agree with the oracle."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import markov as mk
+from oracle import schedule as sc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_1303_5164_gb300 import build, kernelet
+    build.build()
+    return kernelet
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(kl_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(K):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = C.CDLL(K.lib_path())
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    bound = {s[0] for s in K.SIGNATURES}
+    assert names == bound, names ^ bound
+
+
+def test_errors_without_gpu(K):
+    L = K.lib()
+    assert L.kl_abi_version() == 1
+    assert L.kl_strerror(K.KL_EINVAL) == b"invalid argument"
+    out = C.c_void_p()
+    cfg = K.config_default()
+    cfg.model_states = 5
+    assert L.kl_create(C.byref(cfg), None, C.byref(out)) == K.KL_EINVAL
+    assert L.kl_submit(None, None, None) == K.KL_EINVAL
+    assert L.kl_drain(None, 0) == K.KL_EINVAL
+    # shape queries are host-only
+    a = K.kl_args_triad(16, 32, 48, 3.0, 0, 3 * 4096 + 7)
+    sh = K.tenant_shape(K.KL_T_TRIAD, a)
+    assert tuple(sh.grid) == (4, 1, 1) and sh.nstages == 1 and sh.total_blocks == 4
+    bad = K.kl_args_triad(17, 32, 48, 3.0, 0, 100)          # misaligned pointer
+    assert L.kl_tenant_shape_of(K.KL_T_TRIAD, C.byref(bad), C.sizeof(bad), C.byref(sh)) == K.KL_EINVAL
+    g = K.kl_args_gemm_f32(16, 32, 48, 128, 130, 64, 0)     # N not a multiple of 4
+    assert L.kl_tenant_shape_of(K.KL_T_GEMM_F32, C.byref(g), C.sizeof(g), C.byref(sh)) == K.KL_EINVAL
+    b = K.kl_args_bitonic(16, 32, 22, 0)
+    sh = K.tenant_shape(K.KL_T_BITONIC, b)
+    assert sh.nstages == 66 and sh.grid[0] == 1024 and sh.total_blocks == 66 * 1024
+    h = K.kl_args_hist256(16, 32, (1 << 26))
+    sh = K.tenant_shape(K.KL_T_HIST256, h)
+    assert sh.nstages == 2 and sh.grid[0] == 1 and sh.total_blocks == 1 + 4096
+
+
+GPU = mk.GPUParams(n_sm=152, n_sched=4, f_sm_hz=1.9e9, dram_bytes_per_s=6753e9)
+
+
+def _kp(K, p: mk.KernelProfile, PUR=0.0, MUR=0.0):
+    q = K.kl_profile()
+    q.R_m, q.f_u, q.m_c, q.m_u, q.L0, q.I_block = p.R_m, p.f_u, p.m_c, p.m_u, p.L0, p.I_block
+    q.PUR, q.MUR, q.warps_per_block, q.valid = PUR, MUR, p.warps_per_block, 1
+    return q
+
+
+def _mp(K):
+    m = K.kl_model_params()
+    m.n_sm, m.n_sched, m.f_sm_hz, m.dram_bytes_per_s = GPU.n_sm, GPU.n_sched, GPU.f_sm_hz, GPU.dram_bytes_per_s
+    m.sector_bytes, m.a0, m.b0 = 32.0, GPU.a0, GPU.b0
+    return m
+
+
+def _rand_prof(rng, f_u=True):
+    # memory-bound to compute-bound kernels, so CP differs between pairs
+    return mk.KernelProfile(R_m=float(rng.choice([0.002, 0.02, 0.1, 0.3])) * float(rng.uniform(0.8, 1.2)),
+                            L0=float(rng.uniform(100, 1200)),
+                            m_c=4.0, m_u=float(rng.choice([8.0, 16.0, 32.0])),
+                            f_u=float(rng.uniform(0.05, 0.9)) if f_u else 0.0,
+                            I_block=float(rng.uniform(100, 20000)), warps_per_block=8)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_model_ipc_matches_oracle(K, seed):
+    rng = np.random.default_rng(seed)
+    for states in (2, 3):
+        pa, pb = _rand_prof(rng), _rand_prof(rng)
+        for warps in ([1], [5], [8], [3, 5], [1, 7], [4, 4]):
+            profs = [pa, pb][:len(warps)]
+            ref, _, _, _ = mk.model_ipc(profs, warps, GPU, three_state=(states == 3))
+            got = K.model_ipc(_mp(K), [_kp(K, p) for p in profs], warps, states)
+            assert np.allclose(np.array(got) / GPU.n_sched, ref, rtol=1e-11, atol=1e-14), (got, ref)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_model_pair_matches_oracle(K, seed):
+    rng = np.random.default_rng(100 + seed)
+    pa, pb = _rand_prof(rng), _rand_prof(rng)
+    for slots in (2, 4, 6):
+        best, evals, (ia, ib) = mk.evaluate_pair(pa, pb, slots, GPU, three_state=True)
+        r = K.model_pair(_mp(K), _kp(K, pa), _kp(K, pb), slots, 3)
+        assert np.allclose(r["solo"], [ia, ib], rtol=1e-11)
+        for e in evals:
+            i = e.bA - 1
+            assert np.isclose(r["cipc_a"][i], e.cipcA, rtol=1e-11)
+            assert np.isclose(r["cipc_b"][i], e.cipcB, rtol=1e-11)
+            assert np.isclose(r["cp"][i], e.cp, rtol=1e-10, atol=1e-13)
+            assert np.isclose(r["dT"][i], e.dT, rtol=1e-9)
+        assert r["best_a"] == best.bA
+
+
+def test_count_pruned_table3(K):
+    gold = os.path.join(ROOT, "tests", "golden")
+    rows = [l.split() for l in open(os.path.join(gold, "c2050_pur_mur.txt")) if not l.startswith("#")]
+    pur = [float(r[1]) for r in rows]
+    mur = [float(r[2]) for r in rows]
+    for am in (0.015, 0.045, 0.06, 0.105, 0.15):
+        for ap in (0.1, 0.4, 0.7, 1.0):
+            assert K.count_pruned(pur, mur, ap, am) == sc.count_pruned(pur, mur, ap, am)
+    assert K.count_pruned(pur, mur, 0.4, 0.015) == 2       # Table 3, first row
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_plan_matches_oracle_greedy(K, seed):
+    rng = np.random.default_rng(200 + seed)
+    kinds = [_rand_prof(rng, f_u=bool(k % 2)) for k in range(4)]
+    pur = rng.uniform(0, 1, 4)
+    mur = rng.uniform(0, 0.3, 4)
+    n = 7
+    types = [int(rng.integers(4)) for _ in range(n)]
+    blocks = [int(rng.integers(20, 5000)) for _ in range(n)]
+    for ap, am in ((-1.0, -1.0), (0.3, 0.1)):
+        ts = [sc.Tenant(kinds[t], b, PUR=pur[t], MUR=mur[t]) for t, b in zip(types, blocks)]
+        model = sc.PairModel(GPU, 4, three_state=True)
+        phases, mksp = sc.greedy_plan(ts, model, None if ap < 0 else ap, None if am < 0 else am)
+        got, gmk = K.plan(_mp(K), [_kp(K, kinds[t], pur[t], mur[t]) for t in range(4)], types, blocks, 4, 3,
+                          alpha_p=ap, alpha_m=am)
+        assert len(got) == len(phases)
+        for (A, B, sa, sb, cpv, cyc), (cs, dur) in zip(got, phases):
+            assert (A, B if B >= 0 else None) == (cs.A, cs.B)
+            assert (sa, sb) == (cs.bA, cs.bB)
+            assert np.isclose(cyc, dur, rtol=1e-9)
+        assert np.isclose(gmk, mksp, rtol=1e-9)

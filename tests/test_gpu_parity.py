@@ -1,0 +1,196 @@
+"""GPU parity: every tenant through the C ABI (co-scheduled with several slice
+sizes, and as plain launches) against the CPU oracle; the two-tenant pair at
+slot ratios 1:3, 1:1, 3:1; a mixed queue where every result equals its
+alone-run and every device co-schedule decision equals the oracle's."""
+import numpy as np
+import pytest
+
+from tests import _expect as X
+from workloads import gen
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # sizes span several blocks/tiles and end in a ragged tail
+    "gather": dict(n=5000),
+    "blackscholes": dict(n=70001),
+    "gemm_f32": dict(M=200, N=132, K=100),
+    "spmv_csr": dict(nrows=5003),
+    "pchase": dict(N=100003, nchasers=1001, hops=37),
+    "triad": dict(n=3 * 4096 + 7),
+    "hist256": dict(n=3 * 16384 + 5),
+    "escape": dict(width=300, height=170, max_iter=64),
+    "bitonic": dict(log2n=14),
+    "matadd": dict(n=256),
+}
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_1303_5164_gb300 import build, kernelet
+    build.build()
+    return kernelet
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_1303_5164_gb300 import tenants
+    return tenants
+
+
+def _runtime(K, **cfg):
+    c = K.config_default()
+    for k, v in cfg.items():
+        setattr(c, k, v)
+    return K.Runtime(c)
+
+
+def _run_alone(K, rt, ten, slice_blocks=0, baseline=None):
+    import torch
+    for v in ten.outputs:
+        ten.bufs[v].fill_(-1)       # poison the outputs
+    torch.cuda.synchronize()
+    h = rt.submit(ten.type, ten.args, slice_blocks=slice_blocks)
+    if baseline is None:
+        rt.launch()
+    else:
+        rt.launch_baseline(baseline, 4)
+    rc = rt.drain()
+    assert rc == 0, K.lib().kl_strerror(rc)
+    assert rt.poll(h) == K.KL_DONE
+    return ten.fetch()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tenant_alone_matches_oracle(K, T, name):
+    inp = gen.gen_tenant(name, 7, 0, **CASES[name])
+    exp = X.expected(name, inp)
+    rt = _runtime(K)
+    ten = T.make(name, inp)
+    total = ten.shape().total_blocks
+    outs = []
+    for sl in sorted({1, 7, max(1, total // 4), int(total)}):
+        got = _run_alone(K, rt, ten, slice_blocks=sl)
+        X.check(name, inp, got, exp)
+        outs.append(got)
+    for mode in (K.KL_BASE_SERIAL, K.KL_BASE_MULTISTREAM):
+        got = _run_alone(K, rt, ten, baseline=mode)
+        X.check(name, inp, got, exp)
+        outs.append(got)
+    # slicing never changes a result: every run is bit-identical to the first
+    for o in outs[1:]:
+        for k in o:
+            assert X.same_bits(o[k], outs[0][k]), (name, k)
+    rt.close()
+
+
+@pytest.mark.parametrize("log2n", [1, 5, 12, 13, 16])
+def test_bitonic_sizes(K, T, log2n):
+    inp = gen.gen_bitonic(7, 1, log2n)
+    rt = _runtime(K)
+    got = _run_alone(K, rt, T.make("bitonic", inp))
+    X.check("bitonic", inp, got, X.expected("bitonic", inp))
+    rt.close()
+
+
+def test_matadd_slices_of_eight(K, T):
+    # Section 4.1: 256x256 add, 16x16 blocks of 16x16 threads, slices of 8 blocks
+    inp = gen.gen_matadd(7, 2, 256)
+    rt = _runtime(K)
+    ten = T.make("matadd", inp)
+    assert tuple(ten.shape().grid) == (256, 1, 1)
+    h = rt.submit(ten.type, ten.args, slice_blocks=8)
+    assert rt.drain() == 0
+    X.check("matadd", inp, ten.fetch(), X.expected("matadd", inp))
+    assert rt.stats(h).slices == 32 and rt.stats(h).blocks == 256
+    rt.close()
+
+
+@pytest.mark.parametrize("slots_a", [1, 2, 3])
+def test_pair_blackscholes_gather_ratios(K, T, slots_a):
+    # 65,536 options and a 2^20 gather, each cut into 4 slices, at 1:3, 1:1, 3:1
+    bs_in = gen.gen_blackscholes(1, 0, 65536)
+    ga_in = gen.gen_gather(1, 1, 1 << 20)
+    rt = _runtime(K, ratio_policy=K.KL_RATIO_FIXED, fixed_slots_a=slots_a, slots_per_sm=4)
+    bs, ga = T.make("blackscholes", bs_in), T.make("gather", ga_in)
+    h0 = rt.submit(bs.type, bs.args, slice_blocks=bs.shape().total_blocks // 4)
+    h1 = rt.submit(ga.type, ga.args, slice_blocks=ga.shape().total_blocks // 4)
+    assert rt.drain() == 0
+    X.check("blackscholes", bs_in, bs.fetch(), X.expected("blackscholes", bs_in))
+    X.check("gather", ga_in, ga.fetch(), X.expected("gather", ga_in))
+    ph = rt.phases()
+    assert (ph[1].A, ph[1].B, ph[1].slots_a, ph[1].slots_b) == (0, 1, slots_a, 4 - slots_a)
+    assert ph[-1].A == -1
+    assert rt.stats(h0).slices == 4 and rt.stats(h1).slices == 4
+    rt.close()
+
+
+MIX_SMALL = {
+    "gemm_f32": dict(M=256, N=192, K=128),
+    "spmv_csr": dict(nrows=20000),
+    "blackscholes": dict(n=100000),
+    "pchase": dict(N=1 << 18, nchasers=4096, hops=64),
+    "triad": dict(n=1 << 20),
+    "hist256": dict(n=1 << 20),
+    "escape": dict(width=256, height=256, max_iter=256),
+    "bitonic": dict(log2n=16),
+}
+
+
+def _oracle_profiles(K, rt):
+    from oracle import markov as mk
+    mp = rt.model_params()
+    gpu = mk.GPUParams(n_sm=mp.n_sm, n_sched=mp.n_sched, f_sm_hz=mp.f_sm_hz,
+                       dram_bytes_per_s=mp.dram_bytes_per_s, sector_bytes=int(mp.sector_bytes),
+                       a0=mp.a0, b0=mp.b0)
+    return gpu
+
+
+def test_mix_alone_equals_in_mix_and_decisions_match_oracle(K, T):
+    from oracle import markov as mk
+    from oracle import schedule as sc
+    rng = np.random.default_rng(2)
+    order = [t for t in MIX_SMALL for _ in range(2)]
+    rng.shuffle(order)
+    inps = [gen.gen_tenant(nm, 2, i, **MIX_SMALL[nm]) for i, nm in enumerate(order)]
+    rt = _runtime(K, slots_per_sm=4)
+    # known model inputs on both sides
+    profs = []
+    for t in range(K.KL_T_COUNT):
+        p = K.kl_profile()
+        p.R_m, p.f_u, p.m_c, p.m_u = 0.02 + 0.03 * t, (0.1 * t) % 0.7, 4.0, 32.0
+        p.L0, p.I_block, p.warps_per_block, p.valid = 500.0 + 40 * t, 300.0 * (t + 1), 8, 1
+        p.PUR, p.MUR = 0.1 * t, 0.05 * (9 - t)
+        profs.append(p)
+    rt.set_profiles(profs)
+    tens = [T.make(nm, x) for nm, x in zip(order, inps)]
+    handles = [rt.submit(t.type, t.args) for t in tens]
+    assert rt.drain() == 0
+    ph = rt.phases()
+    for nm, x, t, h in zip(order, inps, tens, handles):
+        assert rt.poll(h) == K.KL_DONE
+        X.check(nm, x, t.fetch(), X.expected(nm, x))
+    in_mix = [t.fetch() for t in tens]
+    # each tenant alone on a fresh runtime gives the same bits
+    for t, got in zip(tens, in_mix):
+        alone = _run_alone(K, rt, t)
+        for k in got:
+            assert X.same_bits(alone[k], got[k]), (t.name, k)
+    # replay every device decision through the oracle's FindCoSchedule
+    gpu = _oracle_profiles(K, rt)
+    okp = {t: mk.KernelProfile(R_m=p.R_m, L0=p.L0, m_c=p.m_c, m_u=p.m_u, f_u=p.f_u, I_block=p.I_block,
+                               warps_per_block=p.warps_per_block) for t, p in enumerate(profs)}
+    model = sc.PairModel(gpu, rt.run_stats().slots_per_sm, three_state=True)
+    ot = [sc.Tenant(okp[t.type], 1, PUR=profs[t.type].PUR, MUR=profs[t.type].MUR) for t in tens]
+    assert ph[-1].A == -1 and ph[-1].n_pending == 0
+    for p in ph[1:-1]:
+        R = [i for i in range(len(tens)) if (p.pending_mask >> i) & 1]
+        assert len(R) == p.n_pending
+        cs = sc.find_coschedule(R, ot, model)
+        if (cs.A, cs.B) != (p.A, p.B if p.B >= 0 else None):
+            # only a floating-point near-tie may differ
+            assert abs(cs.cp - p.cp) < 1e-9, ((cs.A, cs.B, cs.cp), (p.A, p.B, p.cp))
+        else:
+            assert (cs.bA, cs.bB) == (p.slots_a, p.slots_b)
+            assert abs(cs.cp - p.cp) < 1e-9 * max(1.0, abs(cs.cp))
+    rt.close()
