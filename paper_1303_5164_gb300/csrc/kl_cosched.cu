@@ -218,7 +218,10 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
         ctl.action = kActExit;
       } else {
         const uint32_t seq = ld_acquire(&R->phase_seq);
-        const PhaseDev ph = P[seq];
+        PhaseDev ph;  // published by another CTA: read through L2
+        ph.A = __ldcg(&P[seq].A);
+        ph.B = __ldcg(&P[seq].B);
+        ph.slots_a = __ldcg(&P[seq].slots_a);
         if (ph.A == -1) {
           ctl.action = kActExit;
         } else {

@@ -571,7 +571,16 @@ static int launch_locked(kl_runtime* rt) {
   memcpy(R.cp, rt->cp, sizeof(R.cp));
   memcpy(R.slots_a, rt->slots_a, sizeof(R.slots_a));
   memcpy(R.allowed, rt->allowed, sizeof(R.allowed));
-  for (uint32_t i = 0; i < n; ++i) rt->h_tenants[i] = rt->pending[i].td;
+  // A slice never exceeds the kernel, and the queue counter (which can
+  // overshoot by one slice per CTA when a kernel runs out) stays below 2^32.
+  const uint64_t ctas = (uint64_t)rt->n_sm * rt->slots;
+  for (uint32_t i = 0; i < n; ++i) {
+    TenantDev td = rt->pending[i].td;
+    uint64_t sl = std::min<uint64_t>(td.slice, td.total);
+    while (sl > 1 && (uint64_t)td.total + sl * (ctas + 1) >= (1ull << 32)) sl >>= 1;
+    td.slice = (uint32_t)std::max<uint64_t>(sl, 1);
+    rt->h_tenants[i] = td;
+  }
   PhaseDev first{};
   first.A = -2;
   first.B = -1;
