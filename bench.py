@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Kernel-mix throughput of the co-scheduled runtime on GB300.
+
+Workload (default): the eight-tenant mix — 64 kernels submitted at once, 8 of
+each type in a seeded order: FP32 GEMM 1024^3, CSR SpMV 2^20 rows (power-law
+rows, mean 16 nnz), Black-Scholes 4 Mi options, int32 pointer chase over a
+64 MiB random cycle (65,536 chasers x 256 hops), FP32 triad 64 Mi, 256-bin
+histogram of 64 Mi Zipf(1.1) bytes, escape-time 2048^2 (max 256 iterations),
+bitonic sort of 2^22 uint32. Inputs are seeded synthetic arrays resident in
+HBM (about 10 GB per step, far larger than L2).
+
+One step = the whole hot path for one batch: submit the 64 descriptors,
+plan (CP table, device-side FindCoSchedule), run the persistent co-scheduler,
+retire completions. The same batch is also run as plain launches on 32
+streams (multi-stream) and on one stream (serial FIFO) for the speedups.
+
+Prints one JSON line (rank 0). --impl reference times the CPU oracle instead.
+Multi-GPU: replicas only (every rank runs its own batch; no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kernel-mix throughput (kernels/s) & makespan speedup vs multi-stream on 1 GB300; p99 latency"
+WORKLOAD = ("8-tenant mix, 64 kernels (8 each of FP32 GEMM 1024^3, CSR SpMV 1Mi rows power-law mean 16, "
+            "Black-Scholes 4Mi, pointer-chase 64MiB x 65536 chasers x 256 hops, triad 64Mi, hist256 64Mi "
+            "Zipf(1.1), escape-time 2048^2 max 256, bitonic 2^22), seeded order")
+
+
+# ---------------------------------------------------------------------- inputs
+
+def _gen_one(job):
+    name, cs, ti, size = job
+    from workloads import gen
+    return gen.gen_tenant(name, cs, ti, **size)
+
+
+def mix_jobs(seed: int = 2, copies: int = 8):
+    import numpy as np
+    from paper_1303_5164_gb300.tenants import MIX_TYPES, SIZES_MIX
+    order = [t for t in MIX_TYPES for _ in range(copies)]
+    np.random.default_rng(seed).shuffle(order)
+    return [(nm, seed, i, SIZES_MIX[nm]) for i, nm in enumerate(order)]
+
+
+def generate(jobs, workers: int):
+    # spawn: the pool starts before any CUDA call and shares nothing with it
+    if workers <= 1:
+        return [_gen_one(j) for j in jobs]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        return pool.map(_gen_one, jobs, chunksize=1)
+
+
+# ---------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------- helpers
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _load_profiles(K):
+    """Measured per-type model inputs, if a profile file exists."""
+    path = os.path.join(ROOT, "paper_1303_5164_gb300", "profiles_gb300.json")
+    if not os.path.exists(path):
+        return None, "builtin (not measured)"
+    with open(path) as f:
+        d = json.load(f)
+    profs = []
+    for t, name in enumerate(K.TYPE_NAMES):
+        p = K.kl_profile()
+        e = d.get("types", {}).get(name)
+        if e:
+            for k in ("R_m", "f_u", "m_c", "m_u", "L0", "I_block", "PUR", "MUR"):
+                setattr(p, k, float(e[k]))
+            p.warps_per_block = int(e.get("warps_per_block", 8))
+            p.valid = 1
+        profs.append(p)
+    return profs, d.get("source", path)
+
+
+def cpu_oracle_sample(jobs_inputs):
+    """The CPU oracle on one instance of each tenant type (single thread)."""
+    import numpy as np
+    from oracle import tenants as OT
+    OT.build()
+    seen = {}
+    for (name, inp) in jobs_inputs:
+        if name not in seen:
+            seen[name] = inp
+    t0 = time.perf_counter()
+    for name, inp in seen.items():
+        if name == "gemm_f32":
+            OT.gemm_f32(inp["A"], inp["B"])
+        elif name == "spmv_csr":
+            OT.spmv_csr(inp["rowptr"], inp["col"], inp["val"], inp["x"])
+        elif name == "blackscholes":
+            OT.blackscholes(inp["S"], inp["K"], inp["r"], inp["v"], inp["T"])
+        elif name == "pchase":
+            OT.pchase(inp["next"], inp["start"], inp["hops"])
+        elif name == "triad":
+            OT.triad(inp["b"], inp["c"], inp["s"])
+        elif name == "hist256":
+            OT.hist256(inp["data"])
+        elif name == "escape":
+            OT.escape(inp["width"], inp["height"], inp["max_iter"], inp["x0"], inp["y0"], inp["dx"], inp["dy"])
+        elif name == "bitonic":
+            OT.sort_u32(inp["data"])
+        elif name == "gather":
+            OT.gather(inp["a"], inp["idx"])
+    dt = time.perf_counter() - t0
+    return len(seen), dt, sorted(seen)
+
+
+# ---------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    jobs = mix_jobs()
+    # one instance of each type per step (a bounded sample of the 64-kernel mix)
+    first = {}
+    for j in jobs:
+        first.setdefault(j[0], j)
+    sample = list(first.values())
+    inputs = generate(sample, min(len(sample), os.cpu_count() or 1))
+    pairs = [(j[0], x) for j, x in zip(sample, inputs)]
+    for _ in range(args.warmup):
+        cpu_oracle_sample(pairs)
+    times = []
+    for _ in range(args.steps):
+        n, dt, _ = cpu_oracle_sample(pairs)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    val = n / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "kernels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "CPU oracle (oracle/tenants.c), single thread"},
+            "cpu_baseline": {"value": val, "unit": "kernels/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one instance of each of the {n} kernel types per step, full size"},
+            "e2e": {"value": val, "unit": "kernels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    jobs = mix_jobs()
+    t_gen = time.time()
+    inputs = generate(jobs, max(1, min(len(jobs), (os.cpu_count() or 2) // max(1, world))))
+    t_gen = time.time() - t_gen
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1303_5164_gb300 import build as kb
+    from paper_1303_5164_gb300 import kernelet as K
+    from paper_1303_5164_gb300 import roofline as RF
+    from paper_1303_5164_gb300 import tenants as T
+    kb.build()
+
+    names = [j[0] for j in jobs]
+    tens = [T.make(nm, x) for nm, x in zip(names, inputs)]
+    stream = torch.cuda.current_stream()
+    cfg = K.config_default()
+    cfg.device = local
+    cfg.max_tenants = 1024
+    rt = K.Runtime(cfg, stream=stream.cuda_stream)
+    hbm_gbs, peak_src = _measured_peaks()
+    mp_ = rt.model_params()
+    mp_.dram_bytes_per_s = hbm_gbs * 1e9
+    rt.set_model_params(mp_)
+    profs, prof_src = _load_profiles(K)
+    if profs:
+        rt.set_profiles(profs)
+
+    def submit_all():
+        return [rt.submit(t.type, t.args) for t in tens]
+
+    def step_cosched():
+        hs = submit_all()
+        rt.launch()
+        rc = rt.drain()
+        if rc != 0:
+            raise RuntimeError(f"co-scheduled run failed: {K.lib().kl_strerror(rc).decode()}")
+        return hs
+
+    def step_base(mode, ns):
+        hs = submit_all()
+        rt.launch_baseline(mode, ns)
+        rc = rt.drain()
+        if rc != 0:
+            raise RuntimeError(f"baseline run failed: {rc}")
+        return hs
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, collect=None):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            hs = fn()
+            if collect:
+                collect(hs)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step_cosched()
+        step_base(K.KL_BASE_MULTISTREAM, args.nstreams)
+        step_base(K.KL_BASE_SERIAL, 1)
+
+    lat_co, kern_ns, phases_n = [], [], []
+
+    def col_co(hs):
+        rs = rt.run_stats()
+        kern_ns.append(rs.kernel_ns)
+        phases_n.append(rs.n_phases)
+        for h in hs:
+            s = rt.stats(h)
+            lat_co.append((s.t_end_ns - s.t_launch_ns) / 1e6)
+
+    lat_ms = []
+
+    def col_ms(hs):
+        for h in hs:
+            lat_ms.append(rt.stats(h).t_end_ns / 1e6)
+
+    with ClockSampler(local) as clk:
+        ms_co = timed(step_cosched, args.steps, col_co)
+    clocks = clk.summary()
+    ms_ms = timed(lambda: step_base(K.KL_BASE_MULTISTREAM, args.nstreams), args.steps, col_ms)
+    ms_se = timed(lambda: step_base(K.KL_BASE_SERIAL, 1), args.steps)
+
+    n = len(tens)
+    value = world * n / (ms_co / 1e3)
+
+    # roofline of the dominant (only) kernel: the persistent co-scheduler
+    esc_iters = {}
+    for t in tens:
+        if t.name == "escape":
+            esc_iters[id(t)] = int(t.bufs["count"].to(torch.int64).sum().item())
+    bytes_mix = sum(RF.algo_bytes(nm, x) for nm, x in zip(names, inputs))
+    flops_mix = sum(RF.fp32_flops(nm, x, esc_iters.get(id(t))) for nm, x, t in zip(names, inputs, tens))
+    kern_ms = statistics.median(kern_ns) / 1e6
+    achieved = bytes_mix / (kern_ms / 1e3) / 1e9
+    f_sm = (clocks.get("sm_mhz") or 1900.0) * 1e6
+    t_roof = max(bytes_mix / (hbm_gbs * 1e9), flops_mix / RF.fp32_peak_flops(mp_.n_sm, f_sm))
+
+    # end to end through the public API with host buffers: H2D inputs, run, D2H outputs
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        h2d = d2h = 0
+        for t in tens:
+            ins = {k: v for k, v in t.bufs.items() if k not in t.outputs}
+            pin_in = {k: v.cpu().pin_memory() for k, v in ins.items()}
+            pin_out = {k: torch.empty(t.bufs[k].shape, dtype=t.bufs[k].dtype, pin_memory=True)
+                       for k in t.outputs}
+            h2d += sum(v.numel() * v.element_size() for v in pin_in.values())
+            d2h += sum(v.numel() * v.element_size() for v in pin_out.values())
+            pinned.append((t, pin_in, pin_out))
+
+        def step_e2e():
+            for t, pin_in, _ in pinned:
+                for k, v in pin_in.items():
+                    t.bufs[k].copy_(v, non_blocking=True)
+            hs = step_cosched()
+            for t, _, pin_out in pinned:
+                for k, v in pin_out.items():
+                    v.copy_(t.bufs[k], non_blocking=True)
+            stream.synchronize()
+            return hs
+
+        step_e2e()
+        ms_e2e = timed(step_e2e, max(2, args.steps // 2))
+        e2e = {"value": world * n / (ms_e2e / 1e3), "unit": "kernels/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+        del pinned
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        k, dt, kinds = cpu_oracle_sample(list(zip(names, inputs)))
+        cpu = {"value": k / dt, "unit": "kernels/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full-size instance of each of the {k} kernel types ({', '.join(kinds)}), "
+                         f"single thread, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "kernels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_co, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "kernels_per_step": n, "l2": "inputs larger than L2 (about "
+                       f"{bytes_mix / 1e9:.1f} GB touched per step)", "slots_per_sm": rt.run_stats().slots_per_sm,
+                       "multistream_streams": args.nstreams, "profiles": prof_src,
+                       "parallelism": f"replicas x{world}"},
+            "speedup_vs_multistream": ms_ms / ms_co, "speedup_vs_serial": ms_se / ms_co,
+            "multistream_kernels_per_s": world * n / (ms_ms / 1e3), "serial_kernels_per_s": world * n / (ms_se / 1e3),
+            "makespan_ms": {"cosched": ms_co, "multistream": ms_ms, "serial": ms_se},
+            "latency_ms": {"cosched_p50": _pct(lat_co, 50), "cosched_p99": _pct(lat_co, 99),
+                           "multistream_p50": _pct(lat_ms, 50), "multistream_p99": _pct(lat_ms, 99)},
+            "mix_roofline": {"t_roof_ms": t_roof * 1e3, "frac": (t_roof * 1e3) / kern_ms,
+                             "algo_bytes": bytes_mix, "fp32_flops": flops_mix},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": achieved / hbm_gbs, "traffic": None,
+                         "kernel": "cosched_kernel", "kernel_ms": kern_ms,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                         else "fallback 6800 GB/s"},
+            "phases_per_run": statistics.median(phases_n) if phases_n else None,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
+            "input_gen_s": round(t_gen, 1),
+        }
+        print(json.dumps(line))
+    rt.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nstreams", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -137,7 +137,7 @@ typedef struct {            /* KL_T_TRIAD: 4096 elements per block             *
 } kl_args_triad;
 
 typedef struct {            /* KL_T_HIST256: stage 0 = 1 block clears hist;    */
-    const uint8_t* data;    /* [n] 16B   stage 1 = 16384 bytes per block        */
+    const uint8_t* data;    /* [n] 16B   stage 1 = 32768 bytes per block        */
     uint32_t* hist;         /* [256]                                           */
     uint64_t n;
 } kl_args_hist256;
@@ -196,6 +196,12 @@ typedef enum {
     KL_RATIO_FIXED = 2          /* kl_config.fixed_slots_a slots for K1           */
 } kl_ratio_policy;
 
+/* kl_config.flags */
+#define KL_CFG_BACKFILL 1u  /* a slot that neither kernel of the current co-schedule
+                               can use (stage barrier, spread rule, re-plan in
+                               flight) runs a slice of another pending kernel;
+                               default on */
+
 typedef struct {
     int32_t device;                 /* CUDA ordinal (default 0)                     */
     uint32_t slots_per_sm;          /* co-scheduler CTAs per SM; 0 = occupancy limit */
@@ -206,7 +212,7 @@ typedef struct {
     uint64_t device_wait_limit_ns;  /* bound on every device spin (default 2 s)     */
     uint64_t mem_cap_bytes;         /* admission cap on summed footprints (0 = none) */
     double alpha_p, alpha_m;        /* pruning thresholds; negative = no pruning    */
-    uint32_t flags;                 /* reserved, 0                                  */
+    uint32_t flags;                 /* KL_CFG_* bits                                */
     uint32_t reserved;
 } kl_config;
 
@@ -263,6 +269,10 @@ typedef struct {
     uint32_t pad;
     uint64_t t_launch_ns;       /* device globaltimer at the first CTA            */
     uint64_t t_end_ns;          /* device globaltimer at the last completion      */
+    uint64_t kernel_ns;         /* CUDA-event time of the persistent launch (co-
+                                   scheduled run) or of the fork/join (baseline) */
+    uint64_t run_ns;            /* CUDA-event time from the run's first copy to
+                                   its last (descriptors in, results out)        */
 } kl_run_stats;
 
 typedef enum { KL_BASE_SERIAL = 0, KL_BASE_MULTISTREAM = 1 } kl_baseline_mode;

@@ -64,14 +64,19 @@ __device__ __forceinline__ void set_error(RunDev* R, int32_t code, uint32_t info
   if (atomicCAS(reinterpret_cast<int*>(&R->error), 0, code) == 0) R->error_info = info;
 }
 
-// Thread 0 only: try to take the next slice of tenant t.
-__device__ __forceinline__ int try_pull(TenantDev* T, int32_t t, uint32_t& g0, uint32_t& g1) {
+// Thread 0 only: try to take the next slice of tenant t. `rank` is this CTA's
+// position among the slots of its SM that serve t: while the stage has fewer
+// blocks left than rank * numSM, the slot leaves them to lower ranks, so a
+// kernel with few blocks spreads one per SM instead of stacking on some SMs.
+__device__ __forceinline__ int try_pull(TenantDev* T, int32_t t, uint32_t rank, uint32_t n_sm, uint32_t& g0,
+                                        uint32_t& g1) {
   TenantDev& d = T[t];
   const uint32_t total = d.total;
   uint32_t n = ld_relaxed(&d.next);
   if (n >= total) return kExhausted;
   tn::Stage st = tn::stage_of(d.type, d.args, n);
   if (st.begin > ld_relaxed(&d.done)) return kBlocked;  // previous stage still running
+  if ((uint64_t)rank * n_sm >= (uint64_t)(st.end - n)) return kBlocked;
   uint32_t a = atomicAdd(&d.next, d.slice);
   if (a >= total) return kExhausted;
   g0 = a;
@@ -98,6 +103,8 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
   for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
   uint32_t npend = 0;
   unsigned long long pmask = 0ull;
+  int32_t lowp[6];
+  uint32_t nlow = 0;
   const uint32_t n = R->n_tenants;
   for (uint32_t base = 0; base < n; base += 32) {
     const uint32_t i = base + lane;
@@ -110,6 +117,7 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
     const uint32_t pb = __ballot_sync(0xffffffffu, pend);
     npend += __popc(pb);
     if (base < 64) pmask |= (unsigned long long)pb << base;
+    for (uint32_t m = pb; m && nlow < 6; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
 #pragma unroll
     for (int t = 0; t < KL_T_COUNT; ++t) {
       uint32_t m = __ballot_sync(0xffffffffu, pend && ty == (uint32_t)t);
@@ -171,6 +179,9 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
       }
     }
   }
+  for (int f = 0; f < 4; ++f) ph.fill[f] = -1;
+  for (uint32_t f = 0, c = 0; f < nlow && c < 4; ++f)
+    if (lowp[f] != ph.A && lowp[f] != ph.B) ph.fill[c++] = lowp[f];
   const uint32_t seq = seq_old + 1;
   if (seq >= R->max_phases) {
     set_error(R, KL_EOVERFLOW, seq);
@@ -206,6 +217,8 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
   }
   __syncthreads();
   const uint32_t slot = s_slot;
+  const uint32_t S = R->slots;
+  const uint32_t n_sm = gridDim.x / S;
   const unsigned long long limit = R->wait_limit_ns;
   unsigned long long wait_since = 0;
   uint32_t backoff = 32;
@@ -231,8 +244,10 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
             const bool mine_is_b = ph.B >= 0 && slot >= ph.slots_a;
             const int32_t t1 = mine_is_b ? ph.B : ph.A;
             const int32_t t2 = mine_is_b ? ph.A : ph.B;
+            const uint32_t rank1 = mine_is_b ? slot - ph.slots_a : slot;
+            const uint32_t rank2 = mine_is_b ? slot : slot + (S - ph.slots_a);
             uint32_t g0 = 0, g1 = 0;
-            int r = try_pull(T, t1, g0, g1);
+            int r = try_pull(T, t1, rank1, n_sm, g0, g1);
             if (r == kPulled) {
               ctl.action = kActRun;
               ctl.tenant = t1;
@@ -250,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
                 ctl.seq = seq;
                 ctl.trigger = trig;
               } else if (t2 >= 0) {
-                int r2 = try_pull(T, t2, g0, g1);
+                int r2 = try_pull(T, t2, rank2, n_sm, g0, g1);
                 if (r2 == kPulled) {
                   ctl.action = kActRun;
                   ctl.tenant = t2;
@@ -269,6 +284,23 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
             ctl.seq = seq;
             ctl.trigger = trig;
           }
+          // backfill: the pair cannot use this slot right now (stage barrier,
+          // spread rule, re-plan in flight), so take a slice of another
+          // pending kernel instead of idling
+          if (ctl.action == kActWait && (R->flags & KL_CFG_BACKFILL) && ph.A >= 0) {
+            for (int f = 0; f < 4; ++f) {
+              const int32_t c = __ldcg(&P[seq].fill[f]);
+              if (c < 0) break;
+              uint32_t g0 = 0, g1 = 0;
+              if (try_pull(T, c, 0u, n_sm, g0, g1) == kPulled) {
+                ctl.action = kActRun;
+                ctl.tenant = c;
+                ctl.g0 = g0;
+                ctl.g1 = g1;
+                break;
+              }
+            }
+          }
         }
       }
       if (ctl.action == kActWait) {
@@ -279,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
           ctl.action = kActExit;
         } else {
           __nanosleep(backoff);
-          backoff = min(backoff * 2, 1024u);
+          backoff = min(backoff * 2, 256u);
         }
       } else {
         wait_since = 0;
@@ -312,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
                 break;
               }
               __nanosleep(bo);
-              bo = min(bo * 2, 1024u);
+              bo = min(bo * 2, 256u);
             }
           }
           __syncthreads();

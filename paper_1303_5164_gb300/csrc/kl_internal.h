@@ -42,8 +42,9 @@ struct PhaseDev {
   int32_t trigger;
   uint32_t n_pending;          // kernels with blocks left when the phase was chosen
   unsigned long long pending;  // bit i: kernel i (i < 64) was pending
+  int32_t fill[4];             // other pending kernels (lowest indices) for backfill
 };
-static_assert(sizeof(PhaseDev) == 48, "PhaseDev layout");
+static_assert(sizeof(PhaseDev) == 64, "PhaseDev layout");
 
 // Run-wide state of one co-scheduled launch.
 struct alignas(128) RunDev {
@@ -52,6 +53,8 @@ struct alignas(128) RunDev {
   uint32_t slots;              // CTAs per SM
   uint32_t max_phases;
   uint32_t n_types;
+  uint32_t flags;              // kl_config.flags
+  uint32_t pad0;
   unsigned long long wait_limit_ns;
   double cp[KL_T_COUNT][KL_T_COUNT];          // CP of (type row as K1, type col as K2)
   uint32_t slots_a[KL_T_COUNT][KL_T_COUNT];   // slots of the K1 (row) kernel

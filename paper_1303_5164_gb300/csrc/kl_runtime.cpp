@@ -135,7 +135,7 @@ uint32_t default_slice(uint32_t type) {
     case KL_T_TRIAD: return 2;
     case KL_T_HIST256: return 2;
     case KL_T_ESCAPE: return 8;
-    case KL_T_BITONIC: return 1;
+    case KL_T_BITONIC: return 2;
     case KL_T_MATADD: return 8;
     default: return 1;
   }
@@ -203,6 +203,7 @@ struct kl_runtime {
   bool in_flight = false;
   uint64_t flight_id = 0;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;   // around the persistent launch
   std::vector<Pending> flight;      // tenants of the in-flight run
   std::vector<cudaEvent_t> tenant_ev;  // baseline per-tenant completion events
   std::map<uint64_t, std::vector<Record>> history;  // retired runs (last few)
@@ -324,6 +325,11 @@ int retire(kl_runtime* rt) {
     rt->last.grid_ctas = rt->slots * rt->n_sm;
     rt->last.t_launch_ns = R.t_launch;
     rt->last.t_end_ns = R.t_end;
+    float ms = 0.f;
+    rt->last.kernel_ns =
+        cudaEventElapsedTime(&ms, rt->ev_k0, rt->ev_k1) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
+    rt->last.run_ns =
+        cudaEventElapsedTime(&ms, rt->ev_start, rt->ev_done) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
   } else {
     // baseline: per-tenant completion from events relative to the fork
     for (uint32_t i = 0; i < n; ++i) {
@@ -342,6 +348,8 @@ int retire(kl_runtime* rt) {
     rt->last.n_tenants = n;
     rt->last.t_launch_ns = 0;
     rt->last.t_end_ns = (uint64_t)((double)ms * 1e6);
+    rt->last.kernel_ns = rt->last.t_end_ns;
+    rt->last.run_ns = rt->last.t_end_ns;
     rt->last_phases.clear();
   }
   record_history(rt, rt->flight_id, std::move(recs));
@@ -408,6 +416,7 @@ extern "C" int kl_config_default(kl_config* c) {
   c->mem_cap_bytes = 0;
   c->alpha_p = -1.0;
   c->alpha_m = -1.0;
+  c->flags = KL_CFG_BACKFILL;
   return KL_OK;
 }
 
@@ -466,6 +475,7 @@ extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime*
   if (cudaMallocHost(&rt->h_run, sizeof(RunDev)) != cudaSuccess) goto fail_mem;
   if (cudaMallocHost(&rt->h_phases, sizeof(PhaseDev) * rt->cap_phases) != cudaSuccess) goto fail_mem;
   if (cudaEventCreate(&rt->ev_start) != cudaSuccess || cudaEventCreate(&rt->ev_done) != cudaSuccess ||
+      cudaEventCreate(&rt->ev_k0) != cudaSuccess || cudaEventCreate(&rt->ev_k1) != cudaSuccess ||
       cudaEventCreateWithFlags(&rt->ev_fork, cudaEventDisableTiming) != cudaSuccess)
     goto fail_cuda;
   // model defaults: device properties, built-in profiles
@@ -511,6 +521,8 @@ extern "C" int kl_destroy(kl_runtime* rt) {
   cudaFreeHost(rt->h_phases);
   if (rt->ev_start) cudaEventDestroy(rt->ev_start);
   if (rt->ev_done) cudaEventDestroy(rt->ev_done);
+  if (rt->ev_k0) cudaEventDestroy(rt->ev_k0);
+  if (rt->ev_k1) cudaEventDestroy(rt->ev_k1);
   if (rt->ev_fork) cudaEventDestroy(rt->ev_fork);
   for (cudaEvent_t e : rt->tenant_ev) cudaEventDestroy(e);
   for (cudaEvent_t e : rt->side_join) cudaEventDestroy(e);
@@ -568,6 +580,7 @@ static int launch_locked(kl_runtime* rt) {
   R.max_phases = std::min(rt->cap_phases, 4 * n + 16);
   R.n_types = KL_T_COUNT;
   R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
+  R.flags = rt->cfg.flags;
   memcpy(R.cp, rt->cp, sizeof(R.cp));
   memcpy(R.slots_a, rt->slots_a, sizeof(R.slots_a));
   memcpy(R.allowed, rt->allowed, sizeof(R.allowed));
@@ -584,13 +597,16 @@ static int launch_locked(kl_runtime* rt) {
   PhaseDev first{};
   first.A = -2;
   first.B = -1;
+  for (int f = 0; f < 4; ++f) first.fill[f] = -1;
   rt->h_phases[0] = first;
   cudaStream_t s = rt->stream;
   rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_tenants, rt->h_tenants, sizeof(TenantDev) * n, cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_phases, rt->h_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
   if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, rt->slots, s) != 0) rc = KL_ECUDA;
+  if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_tenants, rt->d_tenants, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
   if (!rc)

@@ -44,16 +44,18 @@ constexpr int kSpmvRowsPerBlock = 32;
 constexpr int kSpmvLanesPerRow = 8;
 constexpr int kChasersPerBlock = 256;
 constexpr int kTriadPerBlock = 4096;
-constexpr int kHistBytesPerBlock = 16384;
+constexpr int kHistBytesPerBlock = 32768;
 constexpr int kEscapePerBlock = 256;
 constexpr int kBitonicTileLog2 = 12;  // 4096 keys per tile
 
 __host__ __device__ inline uint32_t bitonic_tile_log2(uint32_t L) {
   return L < (uint32_t)kBitonicTileLog2 ? L : (uint32_t)kBitonicTileLog2;
 }
+constexpr uint32_t kBitonicFuse = 4;   // merge levels per global pass (16 keys per thread)
 __host__ __device__ inline uint32_t bitonic_nstages(uint32_t L) {
-  uint32_t P = bitonic_tile_log2(L), d = L - P;
-  return 1 + d * (d + 1) / 2 + d;
+  uint32_t P = bitonic_tile_log2(L), n = 1;
+  for (uint32_t d = 1; d + P <= L; ++d) n += (d + kBitonicFuse - 1) / kBitonicFuse + 1;
+  return n;
 }
 
 // Static shape: stages, blocks per stage, dynamic shared memory.
@@ -118,12 +120,13 @@ __host__ __device__ inline Stage stage_of(uint32_t type, const void* a, uint32_t
 __host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
   switch (type) {
     case KL_T_GEMM_F32: return 2u * (kGemmBM * kGemmBK + kGemmBK * kGemmBN) * 4u;  // 24 KB
-    case KL_T_HIST256: return 8u * 256u * 4u;                                     // 8 KB
-    case KL_T_BITONIC: return (1u << kBitonicTileLog2) * 4u;                      // 16 KB
+    case KL_T_SPMV_CSR: return 256u;                                              // long-row list
+    case KL_T_HIST256: return 256u * 32u * 4u;                                    // 32 KB
+    case KL_T_BITONIC: return ((1u << kBitonicTileLog2) + (1u << (kBitonicTileLog2 - 5))) * 4u;  // padded tile
     default: return 0;
   }
 }
-constexpr uint32_t kMaxTenantSmem = 2u * (kGemmBM * kGemmBK + kGemmBK * kGemmBN) * 4u;
+constexpr uint32_t kMaxTenantSmem = 256u * 32u * 4u;  // largest of the above (histogram)
 
 #ifdef __CUDACC__
 
@@ -373,34 +376,79 @@ __device__ __forceinline__ void gemm_f32_block(const kl_args_gemm_f32& a, uint32
 }
 
 // ------------------------------------------------------------------ CSR SpMV
-// 32 rows per block, 8 lanes per row: lane l of a row sums elements
-// l, l+8, l+16, ... with an ascending fused chain, then a fixed xor butterfly
-// (4, 2, 1) adds the 8 partial sums. The order depends only on the row length.
+// 32 rows per block. A row of at most 128 non-zeros belongs to 8 lanes: lane l
+// sums elements l, l+8, l+16, ... with an ascending fused chain, then a fixed
+// xor butterfly (4, 2, 1) adds the 8 partial sums. A longer row (power-law
+// rows reach 8192) is summed by all 256 threads of the block: thread t takes
+// elements t, t+256, ..., then a fixed butterfly within each warp (16..1) and a
+// fixed pairwise tree over the 8 warps. Either way the order of the additions
+// depends only on the row's length, never on slicing or scheduling.
 
-__device__ __forceinline__ void spmv_csr_block(const kl_args_spmv_csr& a, uint32_t vb) {
+constexpr int kSpmvLong = 128;
+
+__device__ __forceinline__ float spmv_chain(const kl_args_spmv_csr& a, int e, int end, int step, float acc) {
+  // four elements per round, loads issued before any use (predicated past the
+  // row end); the fused chain still runs over e, e+step, e+2*step, ... in order
+  for (; e < end; e += 4 * step) {
+    int c[4];
+    float v[4], x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool ok = e + k * step < end;
+      c[k] = ok ? __ldcs(a.col + e + k * step) : 0;
+      v[k] = ok ? __ldcs(a.val + e + k * step) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = (e + k * step < end) ? __ldg(a.x + c[k]) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (e + k * step < end) acc = __fmaf_rn(v[k], x[k], acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void spmv_csr_block(const kl_args_spmv_csr& a, uint32_t vb, char* smem) {
+  uint32_t* list = reinterpret_cast<uint32_t*>(smem);          // [32] long rows
+  uint32_t* cnt = list + 32;
+  float* red = reinterpret_cast<float*>(list + 40);            // [8] warp partials
   const uint32_t row = vb * kSpmvRowsPerBlock + (threadIdx.x >> 3);
   const int l = threadIdx.x & 7;
-  float acc = 0.0f;
+  if (threadIdx.x == 0) *cnt = 0;
+  __syncthreads();
+  int beg = 0, end = 0;
   if (row < a.nrows) {
-    const int beg = __ldg(a.rowptr + row), end = __ldg(a.rowptr + row + 1);
-    int e = beg + l;
-    for (; e + 24 < end; e += 32) {
-      int c0 = __ldcs(a.col + e), c1 = __ldcs(a.col + e + 8), c2 = __ldcs(a.col + e + 16),
-          c3 = __ldcs(a.col + e + 24);
-      float v0 = __ldcs(a.val + e), v1 = __ldcs(a.val + e + 8), v2 = __ldcs(a.val + e + 16),
-            v3 = __ldcs(a.val + e + 24);
-      float x0 = __ldg(a.x + c0), x1 = __ldg(a.x + c1), x2 = __ldg(a.x + c2), x3 = __ldg(a.x + c3);
-      acc = __fmaf_rn(v0, x0, acc);
-      acc = __fmaf_rn(v1, x1, acc);
-      acc = __fmaf_rn(v2, x2, acc);
-      acc = __fmaf_rn(v3, x3, acc);
-    }
-    for (; e < end; e += 8) acc = __fmaf_rn(__ldcs(a.val + e), __ldg(a.x + __ldcs(a.col + e)), acc);
+    beg = __ldg(a.rowptr + row);
+    end = __ldg(a.rowptr + row + 1);
   }
+  const bool is_long = end - beg > kSpmvLong;
+  float acc = 0.0f;
+  if (!is_long) acc = spmv_chain(a, beg + l, end, 8, 0.0f);
   acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, 4));
   acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, 2));
   acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, 1));
-  if (l == 0 && row < a.nrows) a.y[row] = acc;
+  if (l == 0 && row < a.nrows) {
+    if (!is_long)
+      a.y[row] = acc;
+    else
+      list[atomicAdd(cnt, 1u)] = row;
+  }
+  __syncthreads();
+  const uint32_t nlong = *cnt;
+  for (uint32_t k = 0; k < nlong; ++k) {
+    const uint32_t r = list[k];
+    const int b = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
+    float s = spmv_chain(a, b + threadIdx.x, e, 256, 0.0f);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float p01 = __fadd_rn(red[0], red[1]), p23 = __fadd_rn(red[2], red[3]);
+      float p45 = __fadd_rn(red[4], red[5]), p67 = __fadd_rn(red[6], red[7]);
+      a.y[r] = __fadd_rn(__fadd_rn(p01, p23), __fadd_rn(p45, p67));
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ pointer chase
@@ -442,8 +490,10 @@ __device__ __forceinline__ void triad_block(const kl_args_triad& a, uint32_t vb)
 }
 
 // ------------------------------------------------------------------ histogram
-// stage 0: one block clears the 256 bins; stage 1: each block counts 16 KB into
-// eight per-warp shared sub-histograms, then adds its non-zero bins globally.
+// stage 0: one block clears the 256 bins; stage 1: each block counts 32 KB into
+// 32 lane-private copies of the histogram in shared memory (word bin*32+lane,
+// so the 32 lanes of a warp never share a bank even when they hit the same
+// bin), then adds its non-zero bins to the global histogram.
 
 __device__ __forceinline__ void hist256_block(const kl_args_hist256& a, uint32_t stage, uint32_t vb,
                                               char* smem) {
@@ -451,37 +501,38 @@ __device__ __forceinline__ void hist256_block(const kl_args_hist256& a, uint32_t
     a.hist[threadIdx.x] = 0u;
     return;
   }
-  uint32_t* sh = reinterpret_cast<uint32_t*>(smem);  // [8][256]
+  uint32_t* sh = reinterpret_cast<uint32_t*>(smem);  // [256][32]
+  const uint32_t lane = threadIdx.x & 31;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) sh[w * 256 + threadIdx.x] = 0u;
+  for (int w = 0; w < 8; ++w)
+    reinterpret_cast<uint4*>(sh)[w * 256 + threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
-  uint32_t* mine = sh + (threadIdx.x >> 5) * 256;
   const uint64_t base = (uint64_t)vb * kHistBytesPerBlock;
   if (base + kHistBytesPerBlock <= a.n) {
-    uint4 v[4];
+    uint4 v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
       v[u] = __ldcs(reinterpret_cast<const uint4*>(a.data + base + ((uint64_t)u * 256 + threadIdx.x) * 16));
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      uint32_t w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+    for (int u = 0; u < 8; ++u) {
+      const uint32_t w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        atomicAdd(mine + (w4[q] & 0xffu), 1u);
-        atomicAdd(mine + ((w4[q] >> 8) & 0xffu), 1u);
-        atomicAdd(mine + ((w4[q] >> 16) & 0xffu), 1u);
-        atomicAdd(mine + (w4[q] >> 24), 1u);
+        atomicAdd(sh + (((w4[q] >> 0) & 0xffu) << 5 | lane), 1u);
+        atomicAdd(sh + (((w4[q] >> 8) & 0xffu) << 5 | lane), 1u);
+        atomicAdd(sh + (((w4[q] >> 16) & 0xffu) << 5 | lane), 1u);
+        atomicAdd(sh + ((w4[q] >> 24) << 5 | lane), 1u);
       }
     }
   } else {
     for (uint64_t i = base + threadIdx.x; i < a.n && i < base + kHistBytesPerBlock; i += 256)
-      atomicAdd(mine + a.data[i], 1u);
+      atomicAdd(sh + ((uint32_t)a.data[i] << 5 | lane), 1u);
   }
   __syncthreads();
-  uint32_t s = 0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) s += sh[w * 256 + threadIdx.x];
-  if (s) atomicAdd(a.hist + threadIdx.x, s);
+  uint32_t sum = 0;
+#pragma unroll 8
+  for (uint32_t c = 0; c < 32; ++c) sum += sh[threadIdx.x << 5 | ((c + lane) & 31)];
+  if (sum) atomicAdd(a.hist + threadIdx.x, sum);
 }
 
 // ------------------------------------------------------------------ escape-time
@@ -510,32 +561,40 @@ __device__ __forceinline__ void escape_block(const kl_args_escape& a, uint32_t v
 }
 
 // ------------------------------------------------------------------ bitonic sort
-// Keys n = 2^L, tile = 2^P keys (P = min(L, 12)). Stage list:
-//   0                 : sort every tile in shared memory (all k <= 2^P), in -> out
-//   for lv = P+1 .. L : one global stage per j = 2^(lv-1) .. 2^P (compare
-//                       across tiles), then one shared-memory stage finishing
-//                       j = 2^(P-1) .. 1 of the merge k = 2^lv
-// Direction of a compare-exchange (i, i+j) at merge size k: ascending iff
-// (i & k) == 0 (standard bitonic network on global indices).
+// Keys n = 2^L in tiles of 2^P keys (P = min(L, 12)); merge size k = 2^lv,
+// compare distance j = 2^jl; a compare-exchange (i, i+j) orders ascending iff
+// (i & k) == 0 (the standard bitonic network on global indices). Stages:
+//   0                 : sort every tile in shared memory (lv = 1..P), in -> out
+//   for lv = P+1 .. L : global passes over the levels jl = lv-1 .. P, up to 4
+//                       levels per pass: each thread holds a group of 2^m keys
+//                       spaced 2^jlo apart in registers and runs the m levels
+//                       there; then one shared-memory stage for jl = P-1 .. 0,
+//                       two levels per barrier.
+// Every stage has 2^(L-P) blocks of 4096 (or 2^L) keys.
 
 struct BitonicStep {
-  uint32_t kind;   // 0 tile-full, 1 global (k, j), 2 tile-merge (k)
+  uint32_t kind;   // 0 tile sort, 1 global fused pass, 2 tile merge
   uint32_t lv;     // log2 k
-  uint32_t jl;     // log2 j for global stages
+  uint32_t jhi;    // global pass: highest level
+  uint32_t jlo;    // global pass: lowest level
 };
 
 __host__ __device__ inline BitonicStep bitonic_step(uint32_t L, uint32_t s) {
-  uint32_t P = bitonic_tile_log2(L);
-  if (s == 0) return BitonicStep{0, P, 0};
+  const uint32_t P = bitonic_tile_log2(L);
+  if (s == 0) return BitonicStep{0, P, 0, 0};
   s -= 1;
   for (uint32_t lv = P + 1; lv <= L; ++lv) {
-    uint32_t nglobal = lv - P;
-    if (s < nglobal) return BitonicStep{1, lv, lv - 1 - s};
-    s -= nglobal;
-    if (s == 0) return BitonicStep{2, lv, 0};
+    const uint32_t d = lv - P, npass = (d + kBitonicFuse - 1) / kBitonicFuse;
+    if (s < npass) {
+      const uint32_t jhi = lv - 1 - kBitonicFuse * s;
+      const uint32_t jlo = jhi + 1 >= P + kBitonicFuse ? jhi + 1 - kBitonicFuse : P;
+      return BitonicStep{1, lv, jhi, jlo};
+    }
+    s -= npass;
+    if (s == 0) return BitonicStep{2, lv, 0, 0};
     s -= 1;
   }
-  return BitonicStep{3, 0, 0};  // out of range (never produced for s < nstages)
+  return BitonicStep{3, 0, 0, 0};  // out of range (never produced for s < nstages)
 }
 
 __device__ __forceinline__ void cmpx(uint32_t& x, uint32_t& y, bool asc) {
@@ -544,27 +603,200 @@ __device__ __forceinline__ void cmpx(uint32_t& x, uint32_t& y, bool asc) {
   y = asc ? hi : lo;
 }
 
-// compare-exchange network on a shared tile for merge sizes k in [k_lo, k_hi]
-// with j running from min(k/2, jmax) down to 1
-__device__ __forceinline__ void bitonic_tile(uint32_t* t, uint32_t tile_n, uint64_t gbase,
-                                             uint32_t lv_lo, uint32_t lv_hi, uint32_t jstart_cap) {
-  const uint32_t npairs = tile_n >> 1;
+// One global pass over M levels (jlo .. jlo+M-1) for a 4096-key block. All 16
+// keys of the thread are loaded before any is stored.
+template <int M>
+__device__ __forceinline__ void bitonic_fused(uint32_t* out, uint32_t vb, uint32_t lv, uint32_t jlo) {
+  constexpr int G = 1 << M;                 // keys per group
+  constexpr int PER_THREAD = 16 / G;        // groups per thread (16 keys per thread)
+  const uint64_t k = 1ull << lv;
+  const uint64_t s = 1ull << jlo;
+  uint64_t base[PER_THREAD];
+  uint32_t v[16];
+#pragma unroll
+  for (int u = 0; u < PER_THREAD; ++u) {
+    const uint64_t q = (uint64_t)vb * (4096 / G) + (uint64_t)u * 256 + threadIdx.x;
+    base[u] = ((q >> jlo) << (jlo + M)) | (q & (s - 1));
+#pragma unroll
+    for (int r = 0; r < G; ++r) v[u * G + r] = __ldcg(out + base[u] + r * s);
+  }
+#pragma unroll
+  for (int u = 0; u < PER_THREAD; ++u) {
+    const bool asc = (base[u] & k) == 0;
+#pragma unroll
+    for (int lvl = M - 1; lvl >= 0; --lvl)
+#pragma unroll
+      for (int r = 0; r < G; ++r)
+        if (!(r & (1 << lvl))) cmpx(v[u * G + r], v[u * G + r + (1 << lvl)], asc);
+  }
+#pragma unroll
+  for (int u = 0; u < PER_THREAD; ++u)
+#pragma unroll
+    for (int r = 0; r < G; ++r) out[base[u] + r * s] = v[u * G + r];
+}
+
+// shared-memory tile index with one padding word per 32 (power-of-two strides
+// then fall into different banks)
+__device__ __forceinline__ uint32_t tpad(uint32_t i) { return i + (i >> 5); }
+
+// Shared-memory tile network: merge sizes 2^lv_lo .. 2^lv_hi, distances from
+// min(k/2, jcap) down to 1, two distances per barrier where possible.
+__device__ __forceinline__ void bitonic_tile(uint32_t* t, uint32_t tile_n, uint64_t gbase, uint32_t lv_lo,
+                                             uint32_t lv_hi, uint32_t jcap) {
   for (uint32_t lv = lv_lo; lv <= lv_hi; ++lv) {
     const uint64_t k = 1ull << lv;
-    uint32_t j = (uint32_t)(k >> 1);
-    if (j > jstart_cap) j = jstart_cap;
-    for (; j >= 1; j >>= 1) {
-      for (uint32_t q = threadIdx.x; q < npairs; q += 256) {
-        uint32_t i = (q / j) * 2 * j + (q % j);
-        bool asc = ((gbase + i) & k) == 0;
-        uint32_t x = t[i], y = t[i + j];
-        cmpx(x, y, asc);
-        t[i] = x;
-        t[i + j] = y;
+    uint32_t jl = lv - 1;
+    if ((1u << jl) > jcap) jl = 31 - __clz(jcap);
+    for (int32_t j = (int32_t)jl; j >= 0;) {
+      if (j >= 1) {
+        // distances 2^j and 2^(j-1) together on groups {i, i+h, i+2h, i+3h}
+        const uint32_t hl = (uint32_t)j - 1, h = 1u << hl;
+        for (uint32_t q = threadIdx.x; q < (tile_n >> 2); q += 256) {
+          const uint32_t i = ((q >> hl) << (hl + 2)) | (q & (h - 1));
+          const bool asc = ((gbase + i) & k) == 0;
+          uint32_t a0 = t[tpad(i)], a1 = t[tpad(i + h)], a2 = t[tpad(i + 2 * h)], a3 = t[tpad(i + 3 * h)];
+          cmpx(a0, a2, asc);
+          cmpx(a1, a3, asc);
+          cmpx(a0, a1, asc);
+          cmpx(a2, a3, asc);
+          t[tpad(i)] = a0;
+          t[tpad(i + h)] = a1;
+          t[tpad(i + 2 * h)] = a2;
+          t[tpad(i + 3 * h)] = a3;
+        }
+        j -= 2;
+      } else {
+        for (uint32_t q = threadIdx.x; q < (tile_n >> 1); q += 256) {
+          const uint32_t i = 2 * q;
+          const bool asc = ((gbase + i) & k) == 0;
+          uint32_t x = t[tpad(i)], y = t[tpad(i + 1)];
+          cmpx(x, y, asc);
+          t[tpad(i)] = x;
+          t[tpad(i + 1)] = y;
+        }
+        j = -1;
       }
       __syncthreads();
     }
   }
+}
+
+// Register passes over a 4096-key tile: each of the 256 threads holds 16 keys
+// whose tile positions follow one of three patterns; bit b of the register
+// index r then corresponds to a compare distance, so four consecutive levels
+// of the network run in registers between shared-memory exchanges:
+//   pattern 0: i = t + 256 r                       distances 2048, 1024, 512, 256
+//   pattern 1: i = (t/16) 256 + t%16 + 16 r        distances 128, 64, 32, 16
+//   pattern 2: i = 16 t + r                        distances 8, 4, 2, 1
+template <int PAT>
+__device__ __forceinline__ uint32_t bt_elem(uint32_t t, uint32_t r) {
+  if (PAT == 0) return t + 256u * r;
+  if (PAT == 1) return ((t >> 4) << 8) + (t & 15u) + 16u * r;
+  return 16u * t + r;
+}
+
+template <int PAT>
+__device__ __forceinline__ void bt_load(uint32_t (&v)[16], const uint32_t* t) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = t[tpad(bt_elem<PAT>(threadIdx.x, r))];
+}
+template <int PAT>
+__device__ __forceinline__ void bt_store(const uint32_t (&v)[16], uint32_t* t) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) t[tpad(bt_elem<PAT>(threadIdx.x, r))] = v[r];
+}
+
+// Levels with register-index bits bhi..blo (descending) at merge size k;
+// direction from the global index of each pair.
+template <int PAT>
+__device__ __forceinline__ void bt_levels(uint32_t (&v)[16], int bhi, int blo, uint64_t k, uint64_t gbase) {
+#pragma unroll
+  for (int b = 3; b >= 0; --b) {
+    if (b > bhi || b < blo) continue;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      if (r & (1 << b)) continue;
+      const bool asc = ((gbase + bt_elem<PAT>(threadIdx.x, r)) & k) == 0;
+      cmpx(v[r], v[r | (1 << b)], asc);
+    }
+  }
+}
+
+// Same with one direction for the whole tile (merge sizes above the tile).
+template <bool ASC>
+__device__ __forceinline__ void bt_levels_dir(uint32_t (&v)[16]) {
+#pragma unroll
+  for (int b = 3; b >= 0; --b)
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      if (r & (1 << b)) continue;
+      uint32_t lo = min(v[r], v[r | (1 << b)]), hi = max(v[r], v[r | (1 << b)]);
+      v[r] = ASC ? lo : hi;
+      v[r | (1 << b)] = ASC ? hi : lo;
+    }
+}
+
+// Tile merge for k > 4096: all 12 distances 2048 .. 1, direction uniform.
+__device__ __forceinline__ void bitonic_tile_merge_regs(uint32_t* out, uint32_t* t, uint64_t gbase, uint64_t k) {
+  const bool asc = (gbase & k) == 0;
+  uint32_t v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = __ldcg(out + gbase + bt_elem<0>(threadIdx.x, r));
+  if (asc) bt_levels_dir<true>(v); else bt_levels_dir<false>(v);
+  bt_store<0>(v, t);
+  __syncthreads();
+  bt_load<1>(v, t);
+  if (asc) bt_levels_dir<true>(v); else bt_levels_dir<false>(v);
+  bt_store<1>(v, t);
+  __syncthreads();
+  bt_load<2>(v, t);
+  if (asc) bt_levels_dir<true>(v); else bt_levels_dir<false>(v);
+  uint4* o = reinterpret_cast<uint4*>(out + gbase + 16u * threadIdx.x);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// Full sort of a 4096-key tile (merge sizes 2 .. 4096), keys read from `in`.
+__device__ __forceinline__ void bitonic_tile_sort_regs(const uint32_t* in, uint32_t* out, uint32_t* t,
+                                                       uint64_t gbase) {
+  uint32_t v[16];
+  const uint4* src = reinterpret_cast<const uint4*>(in + gbase + 16u * threadIdx.x);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint4 w = __ldcs(src + q);
+    v[4 * q] = w.x;
+    v[4 * q + 1] = w.y;
+    v[4 * q + 2] = w.z;
+    v[4 * q + 3] = w.w;
+  }
+  // k = 2, 4, 8, 16 inside the thread's 16 consecutive keys
+#pragma unroll
+  for (int lv = 1; lv <= 4; ++lv) bt_levels<2>(v, lv - 1, 0, 1ull << lv, gbase);
+  int pat = 2;  // pattern the registers currently follow
+  for (uint32_t lv = 5; lv <= 12; ++lv) {
+    const uint64_t k = 1ull << lv;
+    if (lv >= 9) {  // distances 2^(lv-1) .. 256
+      bt_store<2>(v, t);
+      __syncthreads();
+      bt_load<0>(v, t);
+      bt_levels<0>(v, (int)lv - 9, 0, k, gbase);
+      pat = 0;
+    }
+    // distances min(2^(lv-1), 128) .. 16
+    if (pat == 0) bt_store<0>(v, t); else bt_store<2>(v, t);
+    __syncthreads();
+    bt_load<1>(v, t);
+    bt_levels<1>(v, (int)(lv >= 9 ? 3 : lv - 5), 0, k, gbase);
+    bt_store<1>(v, t);
+    __syncthreads();
+    bt_load<2>(v, t);
+    bt_levels<2>(v, 3, 0, k, gbase);
+    pat = 2;
+    __syncthreads();  // the next exchange overwrites the tile
+  }
+  uint4* o = reinterpret_cast<uint4*>(out + gbase + 16u * threadIdx.x);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
 __device__ __forceinline__ void bitonic_block(const kl_args_bitonic& a, uint32_t stage, uint32_t vb,
@@ -574,30 +806,32 @@ __device__ __forceinline__ void bitonic_block(const kl_args_bitonic& a, uint32_t
   const uint32_t tile_n = 1u << P;
   const BitonicStep st = bitonic_step(L, stage);
   if (st.kind == 1) {
-    // global stage: 2048 pairs per block (tile_n/2), 8 per thread, coalesced
-    const uint64_t j = 1ull << st.jl, k = 1ull << st.lv;
-    const uint64_t q0 = (uint64_t)vb * (tile_n >> 1);
-    for (uint32_t q = threadIdx.x; q < (tile_n >> 1); q += 256) {
-      uint64_t qq = q0 + q;
-      uint64_t i = (qq / j) * 2 * j + (qq % j);
-      bool asc = (i & k) == 0;
-      uint32_t x = __ldcg(a.out + i), y = __ldcg(a.out + i + j);
-      cmpx(x, y, asc);
-      a.out[i] = x;
-      a.out[i + j] = y;
+    switch (st.jhi - st.jlo + 1) {
+      case 4: bitonic_fused<4>(a.out, vb, st.lv, st.jlo); break;
+      case 3: bitonic_fused<3>(a.out, vb, st.lv, st.jlo); break;
+      case 2: bitonic_fused<2>(a.out, vb, st.lv, st.jlo); break;
+      default: bitonic_fused<1>(a.out, vb, st.lv, st.jlo); break;
     }
     return;
   }
   uint32_t* t = reinterpret_cast<uint32_t*>(smem);
   const uint64_t gbase = (uint64_t)vb * tile_n;
+  if (tile_n == 4096u) {
+    if (st.kind == 0)
+      bitonic_tile_sort_regs(a.in, a.out, t, gbase);
+    else
+      bitonic_tile_merge_regs(a.out, t, gbase, 1ull << st.lv);
+    return;
+  }
+  // small sorts (fewer than 4096 keys): one block, shared-memory network
   const uint32_t* src = st.kind == 0 ? a.in : a.out;
-  for (uint32_t q = threadIdx.x; q < tile_n; q += 256) t[q] = __ldcg(src + gbase + q);
+  for (uint32_t q = threadIdx.x; q < tile_n; q += 256) t[tpad(q)] = __ldcg(src + gbase + q);
   __syncthreads();
   if (st.kind == 0)
     bitonic_tile(t, tile_n, gbase, 1, P, tile_n);
   else
     bitonic_tile(t, tile_n, gbase, st.lv, st.lv, tile_n >> 1);
-  for (uint32_t q = threadIdx.x; q < tile_n; q += 256) a.out[gbase + q] = t[q];
+  for (uint32_t q = threadIdx.x; q < tile_n; q += 256) a.out[gbase + q] = t[tpad(q)];
 }
 
 // ------------------------------------------------------------------ MatrixAdd
@@ -627,7 +861,7 @@ __device__ __forceinline__ void run_block(uint32_t type, const void* args, const
     case KL_T_GATHER: gather_block(load_args<kl_args_gather>(args), vb); break;
     case KL_T_BLACKSCHOLES: blackscholes_block(load_args<kl_args_blackscholes>(args), vb); break;
     case KL_T_GEMM_F32: gemm_f32_block(load_args<kl_args_gemm_f32>(args), vb, smem); break;
-    case KL_T_SPMV_CSR: spmv_csr_block(load_args<kl_args_spmv_csr>(args), vb); break;
+    case KL_T_SPMV_CSR: spmv_csr_block(load_args<kl_args_spmv_csr>(args), vb, smem); break;
     case KL_T_PCHASE: pchase_block(load_args<kl_args_pchase>(args), vb); break;
     case KL_T_TRIAD: triad_block(load_args<kl_args_triad>(args), vb); break;
     case KL_T_HIST256: hist256_block(load_args<kl_args_hist256>(args), st.s, vb, smem); break;

@@ -27,6 +27,7 @@ TYPE_NAMES = ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad
               "escape", "bitonic", "matadd"]
 KL_RATIO_BALANCED, KL_RATIO_MAX_CP, KL_RATIO_FIXED = 0, 1, 2
 KL_BASE_SERIAL, KL_BASE_MULTISTREAM = 0, 1
+KL_CFG_BACKFILL = 1
 
 P = C.c_void_p
 U32, U64, I32, F32, F64 = C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
@@ -120,7 +121,8 @@ class kl_tenant_stats(C.Structure):
 
 class kl_run_stats(C.Structure):
     _fields_ = [("n_tenants", U32), ("n_phases", U32), ("error", I32), ("slots_per_sm", U32),
-                ("grid_ctas", U32), ("pad", U32), ("t_launch_ns", U64), ("t_end_ns", U64)]
+                ("grid_ctas", U32), ("pad", U32), ("t_launch_ns", U64), ("t_end_ns", U64),
+                ("kernel_ns", U64), ("run_ns", U64)]
 
 
 class KLError(RuntimeError):

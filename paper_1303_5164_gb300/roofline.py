@@ -1,0 +1,60 @@
+"""Algorithmic work per tenant instance, for roofline fractions.
+
+Bytes are the DRAM traffic the computation cannot avoid (every input read
+once, every output written once); FLOPs count the binary32 operations of the
+tenant's written definition. Measured traffic well above these means re-reads.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# binary32 operations per Black-Scholes option in the written recipe (two CND
+# evaluations, one exp and one log of the Cody-Waite / atanh recipes)
+BS_FLOPS_PER_OPTION = 93
+ESCAPE_FLOPS_PER_ITER = 7
+
+
+def algo_bytes(name: str, inp: dict) -> int:
+    if name == "gather":
+        return 12 * inp["n"]
+    if name == "blackscholes":
+        return 28 * inp["n"]
+    if name == "gemm_f32":
+        return 4 * (inp["M"] * inp["K"] + inp["K"] * inp["N"] + inp["M"] * inp["N"])
+    if name == "spmv_csr":
+        return 8 * inp["nnz"] + 4 * (inp["nrows"] + 1) + 4 * inp["nrows"] + 4 * inp["ncols"]
+    if name == "pchase":
+        return 4 * inp["hops"] * inp["nchasers"] + 8 * inp["nchasers"]
+    if name == "triad":
+        return 12 * inp["n"]
+    if name == "hist256":
+        return inp["n"] + 1024
+    if name == "escape":
+        return 4 * inp["width"] * inp["height"]
+    if name == "bitonic":
+        return 8 * inp["n"]
+    if name == "matadd":
+        return 12 * inp["n"] * inp["n"]
+    raise ValueError(name)
+
+
+def fp32_flops(name: str, inp: dict, escape_iters: int | None = None) -> int:
+    """binary32 operations on the FP32 pipe (integer tenants: 0)."""
+    if name == "gemm_f32":
+        return 2 * inp["M"] * inp["N"] * inp["K"]
+    if name == "blackscholes":
+        return BS_FLOPS_PER_OPTION * inp["n"]
+    if name == "spmv_csr":
+        return 2 * inp["nnz"]
+    if name == "triad":
+        return 2 * inp["n"]
+    if name == "escape":
+        return ESCAPE_FLOPS_PER_ITER * int(escape_iters or 0)
+    if name == "matadd":
+        return inp["n"] * inp["n"]
+    return 0
+
+
+def fp32_peak_flops(n_sm: int, f_sm_hz: float) -> float:
+    """FFMA peak: 128 binary32 lanes per SM, 2 operations per fused multiply-add."""
+    return n_sm * 128 * 2 * f_sm_hz

@@ -37,11 +37,16 @@ def expected(name: str, inp: dict) -> dict:
     raise ValueError(name)
 
 
+SPMV_LONG = 128
+
+
 def spmv_bound(rowptr, asum):
-    """|y_gpu - y_exact| <= (ceil(len/8) + 3 + 1) u sum|a x| per row: each of the
-    8 lanes runs a fused chain over ceil(len/8) terms, then 3 butterfly adds."""
+    """|y_gpu - y_exact| <= depth * u * sum|a x| per row (Higham's bound for a
+    summation tree of that depth): rows up to 128 non-zeros run 8 fused chains
+    of ceil(len/8) terms and 3 butterfly adds; longer rows run 256 chains of
+    ceil(len/256) terms, a 5-level warp butterfly and a 3-level tree."""
     deg = np.diff(rowptr.astype(np.int64))
-    depth = np.ceil(deg / 8.0) + 4.0
+    depth = np.where(deg > SPMV_LONG, np.ceil(deg / 256.0) + 9.0, np.ceil(deg / 8.0) + 4.0)
     return depth * U * asum
 
 

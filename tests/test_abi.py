@@ -61,10 +61,10 @@ def test_errors_without_gpu(K):
     assert L.kl_tenant_shape_of(K.KL_T_GEMM_F32, C.byref(g), C.sizeof(g), C.byref(sh)) == K.KL_EINVAL
     b = K.kl_args_bitonic(16, 32, 22, 0)
     sh = K.tenant_shape(K.KL_T_BITONIC, b)
-    assert sh.nstages == 66 and sh.grid[0] == 1024 and sh.total_blocks == 66 * 1024
+    assert sh.nstages == 29 and sh.grid[0] == 1024 and sh.total_blocks == 29 * 1024
     h = K.kl_args_hist256(16, 32, (1 << 26))
     sh = K.tenant_shape(K.KL_T_HIST256, h)
-    assert sh.nstages == 2 and sh.grid[0] == 1 and sh.total_blocks == 1 + 4096
+    assert sh.nstages == 2 and sh.grid[0] == 1 and sh.total_blocks == 1 + 2048
 
 
 GPU = mk.GPUParams(n_sm=152, n_sched=4, f_sm_hz=1.9e9, dram_bytes_per_s=6753e9)

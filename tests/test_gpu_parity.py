@@ -18,7 +18,7 @@ CASES = {
     "spmv_csr": dict(nrows=5003),
     "pchase": dict(N=100003, nchasers=1001, hops=37),
     "triad": dict(n=3 * 4096 + 7),
-    "hist256": dict(n=3 * 16384 + 5),
+    "hist256": dict(n=3 * 32768 + 5),
     "escape": dict(width=300, height=170, max_iter=64),
     "bitonic": dict(log2n=14),
     "matadd": dict(n=256),
