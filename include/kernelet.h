@@ -366,6 +366,40 @@ int kl_plan(const kl_model_params* gp, const kl_profile* type_profiles, uint32_t
 int kl_count_pruned(const double* pur, const double* mur, uint32_t n, double alpha_p,
                     double alpha_m, uint32_t* out);
 
+/* ------------------------------------------------- allocation-free variant
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory where they run work: frameworks whose caching
+ * allocator has reserved the device memory up front (a raw cudaMalloc then
+ * fails or fragments their pool), and latency-critical threads that must not
+ * call cudaMalloc / cudaFree because those calls can synchronize the device.
+ *
+ * kl_run_noalloc runs descs[0..n) as ONE co-scheduled launch of the same
+ * persistent kernel as kl_launch and waits for it on `cuda_stream` (a
+ * cudaStream_t, may be NULL). It calls no cudaMalloc, cudaFree or other
+ * allocating routine: the device queue, run state and phase log live in a
+ * fixed file-scope device array of the library (about 37 KB, held by every
+ * GPU that loads the library until the process exits), and the host-side
+ * descriptor image lives on the caller's stack (about 19 KB).
+ *   descs, n        kernel descriptors as for kl_submit; 1 <= n <=
+ *                   KL_NOALLOC_MAX_TENANTS, else KL_EOVERFLOW (n = 0: KL_EINVAL)
+ *   cp_table        NULL, or KL_T_COUNT x KL_T_COUNT CP values by (type of the
+ *                   lower-index kernel, type of the other) for the device planner;
+ *                   NULL = all equal (pairs in submission order)
+ *   slots_a_table   NULL, or slots per SM for the lower-index kernel of each
+ *                   type pair (clamped to 1..slots-1); NULL = even split
+ *   wait_limit_ns   bound of every device-side wait (0 = 2 s)
+ *   states          NULL, or n entries receiving KL_DONE / KL_ERROR per kernel
+ * Returns KL_OK when every kernel completed, else a kl_status.
+ * The first call on each device takes the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Every call shares the array, which keeps the last
+ * call's contents (each call rewrites what must start at zero); calls whose
+ * GPU work overlaps race on it and must not be issued concurrently. */
+#define KL_NOALLOC_MAX_TENANTS 64
+int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const double* cp_table,
+                   const uint32_t* slots_a_table, void* cuda_stream, uint64_t wait_limit_ns,
+                   int32_t* states);
+
 const char* kl_strerror(int code);
 int kl_abi_version(void);
 

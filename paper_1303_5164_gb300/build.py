@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libkernelet.so")
 
-SOURCES = ["kl_cosched.cu", "kl_native.cu", "kl_runtime.cpp", "kl_model.cpp"]
+SOURCES = ["kl_cosched.cu", "kl_native.cu", "kl_noalloc.cu", "kl_runtime.cpp", "kl_model.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

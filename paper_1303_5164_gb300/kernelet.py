@@ -163,7 +163,10 @@ SIGNATURES = [
                           C.POINTER(U64), U32, U32, U32, U32, F64, F64, C.POINTER(kl_phase),
                           C.POINTER(F64), U32, C.POINTER(U32), C.POINTER(F64)]),
     ("kl_count_pruned", C.c_int, [C.POINTER(F64), C.POINTER(F64), U32, F64, F64, C.POINTER(U32)]),
+    ("kl_run_noalloc", C.c_int, [C.POINTER(kl_kernel_desc), U32, C.POINTER(F64), C.POINTER(U32), P, U64,
+                                 C.POINTER(I32)]),
 ]
+KL_NOALLOC_MAX_TENANTS = 64
 
 
 def lib_path() -> str:
@@ -244,6 +247,21 @@ def tenant_shape(type_: int, args) -> kl_tenant_shape:
     sh = kl_tenant_shape()
     check(lib().kl_tenant_shape_of(type_, C.byref(args), C.sizeof(args), C.byref(sh)), "kl_tenant_shape_of")
     return sh
+
+
+def make_desc(type_: int, args, slice_blocks: int = 0, footprint: int = 0) -> kl_kernel_desc:
+    """Descriptor of one kernel with the tenant's own launch shape."""
+    sh = tenant_shape(type_, args)
+    d = kl_kernel_desc()
+    d.type = type_
+    d.grid[:] = list(sh.grid)
+    d.block[:] = [KL_BLOCK_THREADS, 1, 1]
+    d.smem_bytes = sh.smem_bytes
+    d.slice_blocks = slice_blocks
+    d.args = C.cast(C.byref(args), P)
+    d.args_size = C.sizeof(args)
+    d.footprint_bytes = footprint
+    return d
 
 
 def config_default() -> kl_config:
