@@ -116,6 +116,62 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons every 5 ms through NVML (ctypes), for
+    timed regions shorter than nvidia-smi's sampling period."""
+
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device: int):
+        import ctypes
+        import threading
+        self.ok = False
+        self.samples = []
+        self._stop = threading.Event()
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.nvml.nvmlDeviceGetHandleByIndex_v2(device, ctypes.byref(self.h)) != 0:
+                return
+            mx = ctypes.c_uint()
+            self.max_mhz = mx.value if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 else None
+            self.ok = True
+        except Exception:
+            self.ok = False
+        self._thr = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        import ctypes
+        mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz)) == 0:
+                r = rs.value if self.nvml.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((mhz.value, r))
+            time.sleep(0.005)
+
+    def __enter__(self):
+        if self.ok:
+            self._thr.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self._thr.join(timeout=2)
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return None
+        mask = 0
+        for _, r in self.samples:
+            mask |= r
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(v for b, v in self.BITS.items() if mask & b), "samples": len(self.samples)}
+
+
 # ---------------------------------------------------------------------- helpers
 
 def _pct(xs, q):
@@ -135,11 +191,13 @@ def _measured_peaks():
     return 6800.0, "fallback"
 
 
-def _load_profiles(K):
-    """Measured per-type model inputs, if a profile file exists."""
-    path = os.path.join(ROOT, "paper_1303_5164_gb300", "profiles_gb300.json")
-    if not os.path.exists(path):
-        return None, "builtin (not measured)"
+PROFILES = os.path.join(ROOT, "paper_1303_5164_gb300", "profiles_gb300.json")
+
+
+def _load_profiles(K, path=PROFILES):
+    """Measured per-type model inputs and slice sizes, if a profile file exists."""
+    if not path or not os.path.exists(path):
+        return None, None
     with open(path) as f:
         d = json.load(f)
     profs = []
@@ -150,9 +208,10 @@ def _load_profiles(K):
             for k in ("R_m", "f_u", "m_c", "m_u", "L0", "I_block", "PUR", "MUR"):
                 setattr(p, k, float(e[k]))
             p.warps_per_block = int(e.get("warps_per_block", 8))
+            p.slice_blocks = int(d.get("slices", {}).get(name, 0))
             p.valid = 1
         profs.append(p)
-    return profs, d.get("source", path)
+    return profs, d
 
 
 def cpu_oracle_sample(jobs_inputs):
@@ -256,9 +315,16 @@ def run_ours(args):
     mp_ = rt.model_params()
     mp_.dram_bytes_per_s = hbm_gbs * 1e9
     rt.set_model_params(mp_)
-    profs, prof_src = _load_profiles(K)
+    profs, prof_doc = _load_profiles(K, None if args.profiles == "none" else PROFILES)
+    model_info = {"profiles": "built-in (not measured)"}
     if profs:
         rt.set_profiles(profs)
+        mp_.a0, mp_.b0 = prof_doc.get("a0", 1.0), prof_doc.get("b0", 0.0)
+        rt.set_model_params(mp_)
+        model_info = {"profiles": prof_doc.get("source"), "a0": mp_.a0, "b0": mp_.b0,
+                      "solo_ipc_mae_per_sm": prof_doc.get("ipc_mae_per_sm"), "ipc_peak_per_sm": 4.0,
+                      "slices": prof_doc.get("slices")}
+    prof_src = model_info["profiles"]
 
     def submit_all():
         return [rt.submit(t.type, t.args) for t in tens]
@@ -322,9 +388,12 @@ def run_ours(args):
         for h in hs:
             lat_ms.append(rt.stats(h).t_end_ns / 1e6)
 
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk, NvmlSampler(local) as nv:
         ms_co = timed(step_cosched, args.steps, col_co)
     clocks = clk.summary()
+    nvs = nv.summary()
+    if nvs:
+        clocks = dict(nvs, nvidia_smi=clocks)
     ms_ms = timed(lambda: step_base(K.KL_BASE_MULTISTREAM, args.nstreams), args.steps, col_ms)
     ms_se = timed(lambda: step_base(K.KL_BASE_SERIAL, 1), args.steps)
 
@@ -403,6 +472,7 @@ def run_ours(args):
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback 6800 GB/s"},
             "phases_per_run": statistics.median(phases_n) if phases_n else None,
+            "model": model_info,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
             "input_gen_s": round(t_gen, 1),
         }
@@ -422,6 +492,7 @@ def main():
     ap.add_argument("--nstreams", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profiles", default="measured", choices=["measured", "none"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -228,6 +228,10 @@ typedef struct {
     double PUR, MUR;        /* Section 4.3 utilisation ratios (pruning)          */
     uint32_t warps_per_block;
     uint32_t valid;         /* 0 = no profile for this type                      */
+    uint32_t slice_blocks;  /* blocks per slice for this type (Section 4.1: the
+                               smallest slice whose overhead is within p%);
+                               0 = the runtime's built-in size               */
+    uint32_t pad;
 } kl_profile;
 
 typedef struct {

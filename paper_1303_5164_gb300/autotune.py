@@ -1,0 +1,77 @@
+"""Slice-size selection (Section 4.1): the smallest slice whose overhead is
+within p% (default 2%) of the unsliced execution.
+
+On this runtime a slice is the block range one persistent CTA pulls with one
+atomic; the unsliced reference T_ns is the kernel alone in the co-scheduler
+with one slice per CTA and stage (the fewest pulls that still use every slot).
+For each type, T_s is measured for slices of 1, 2, 4, ... blocks; the chosen
+size is the smallest with T_s / T_ns - 1 <= p (else the fastest measured).
+
+    python -m paper_1303_5164_gb300.autotune --out slices.json [--p 0.02]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def tune(types, p=0.02, reps=3, seed=6):
+    import torch
+    from workloads import gen
+    from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
+    build.build()
+    rt = K.Runtime()
+    S = rt.run_stats().slots_per_sm
+    n_sm = rt.model_params().n_sm
+    out = {"p": p, "slots_per_sm": S, "n_sm": n_sm, "slices": {}, "times_us": {}, "overhead": {}}
+    for i, ty in enumerate(types):
+        inp = gen.gen_tenant(ty, seed, i, **T.SIZES_MIX[ty])
+        t = T.make(ty, inp)
+        sh = t.shape()
+        stage_blocks = int(sh.grid[0]) if ty != "hist256" else int(sh.total_blocks - 1)
+        ref = max(1, math.ceil(stage_blocks / (n_sm * S)))
+        cands = sorted({c for c in (1, 2, 4, 8, 16, 32, 64) if c <= stage_blocks} | {ref})
+
+        def run(sl):
+            best = float("inf")
+            for _ in range(reps + 1):
+                rt.submit(t.type, t.args, slice_blocks=sl)
+                rt.launch()
+                assert rt.drain() == 0
+                best = min(best, rt.run_stats().kernel_ns / 1e3)
+            return best
+
+        times = {c: run(c) for c in cands}
+        tns = times[ref]
+        ok = [c for c in cands if times[c] / tns - 1.0 <= p]
+        chosen = min(ok) if ok else min(times, key=times.get)
+        out["slices"][ty] = chosen
+        out["times_us"][ty] = {str(c): round(v, 2) for c, v in times.items()}
+        out["overhead"][ty] = round(times[chosen] / tns - 1.0, 4)
+        print(ty, "ref", ref, "chosen", chosen, out["times_us"][ty], flush=True)
+        del t
+        torch.cuda.empty_cache()
+    rt.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--p", type=float, default=0.02)
+    ap.add_argument("--types", default="gemm_f32,spmv_csr,blackscholes,pchase,triad,hist256,escape,bitonic")
+    a = ap.parse_args(argv)
+    res = tune(a.types.split(","), a.p)
+    with open(a.out, "w") as f:
+        json.dump(res, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -353,10 +353,11 @@ __global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restr
         const uint32_t ge = min(g1, st.end);
         for (uint32_t b = g; b < ge; ++b) {
           tn::run_block(type, d.args, st, b, smem);
-          __syncthreads();
+          __syncthreads();  // shared memory is reused by the next block
         }
         if (tid == 0) {
-          __threadfence();
+          // a later stage reads what this one wrote: release before counting
+          if (d.nstages > 1) __threadfence();
           const uint32_t cnt = ge - g;
           const uint32_t old = atomicAdd(&d.done, cnt);
           if (old + cnt == d.total) complete_tenant(d, R);

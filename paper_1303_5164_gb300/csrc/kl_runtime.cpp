@@ -548,7 +548,9 @@ extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out
   Pending p;
   memset(&p.td, 0, sizeof(p.td));
   p.td.type = d->type;
-  p.td.slice = d->slice_blocks ? d->slice_blocks : default_slice(d->type);
+  p.td.slice = d->slice_blocks                       ? d->slice_blocks
+                : rt->prof[d->type].slice_blocks ? rt->prof[d->type].slice_blocks
+                                                 : default_slice(d->type);
   p.td.total = (uint32_t)sh.total_blocks;
   p.td.nstages = sh.nstages;
   p.td.index = (uint32_t)rt->pending.size();

@@ -1,13 +1,19 @@
-"""Runs tenants as plain launches (one instance per type, after a warm-up) so
-that an external profiler (ncu) can measure them; also the driver for the
-per-type model inputs of Section 4.4 (R_m, sectors per request, instructions
-per block, IPC, PUR/MUR) when run under ncu with --csv.
+"""Per-type model inputs of Section 4.4 measured on the GPU.
 
-    python -m paper_1303_5164_gb300.profile_tenants [--types a,b] [--mode native|cosched]
-                                                    [--scale 1.0] [--reps 1]
-
---mode cosched runs each type alone through the persistent co-scheduler
-instead (the kernel name is cosched_kernel). --scale shrinks the mix sizes.
+1. Run tenants as plain launches (one instance per type, after a warm-up) so
+   that ncu can count them:
+       ncu --metrics <METRICS> --csv --page raw --log-file m.csv \
+           python -m paper_1303_5164_gb300.profile_tenants
+   --mode cosched runs each type alone through the persistent co-scheduler,
+   --mode mix runs one instance of every type in ONE co-scheduled launch.
+2. Measure the unloaded memory latency L0 (one dependent chain per thread over
+   a random cycle larger than L2, and one inside L2):
+       python -m paper_1303_5164_gb300.profile_tenants --latency lat.json
+3. Turn the counters into kl_profile records (R_m, f_u, m_c/m_u, L0,
+   instructions per block, PUR, MUR), fit the linear latency model's a0, b0 on
+   the solo IPCs with the runtime's own model, and report its IPC error:
+       python -m paper_1303_5164_gb300.profile_tenants --ingest m.csv \
+           --latency-json lat.json --out paper_1303_5164_gb300/profiles_gb300.json
 """
 from __future__ import annotations
 
@@ -40,13 +46,187 @@ def scaled_sizes(name, scale):
     return s
 
 
+METRICS = ",".join([
+    "gpu__time_duration.sum", "sm__cycles_elapsed.avg", "smsp__inst_executed.sum",
+    "smsp__inst_executed_op_global_ld.sum", "smsp__inst_executed_op_ldgsts.sum",
+    "l1tex__t_requests_pipe_lsu_mem_global_op_ld.sum", "l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum",
+    "sm__inst_executed.avg.per_cycle_active", "sm__warps_active.avg.per_cycle_active",
+    "dram__bytes_read.sum", "dram__bytes_write.sum", "launch__grid_size"])
+
+TYPE_OF_KERNEL = {f"native_kernel<{i}>": n for i, n in enumerate(
+    ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256", "escape", "bitonic",
+     "matadd"])}
+
+# working sets at or under half of L2 see the L2 latency, larger ones DRAM's
+L2_RESIDENT = {"gemm_f32", "bitonic", "pchase"}
+
+
+def latency_probe(out_path: str):
+    """ns per dependent load: 256 independent chains (one block) walking a
+    random cycle, 2048 hops each, over 256 MiB (DRAM) and over 4 MiB (L2)."""
+    import json
+    import time
+    import numpy as np
+    import torch
+    from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
+    build.build()
+    rt = K.Runtime()
+    res = {}
+    for label, N in (("dram", 1 << 26), ("l2", 1 << 20)):
+        order = np.random.default_rng(7).permutation(N)
+        nxt = np.empty(N, np.int32)
+        nxt[order] = np.roll(order, -1)
+        hops = 2048
+        inp = dict(next=nxt, start=(np.arange(256) * (N // 256)).astype(np.int32), N=N, nchasers=256, hops=hops)
+        t = T.make("pchase", inp)
+        best = 1e9
+        for _ in range(5):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            rt.submit(t.type, t.args)
+            e0.record()
+            rt.launch_baseline(K.KL_BASE_SERIAL, 1)
+            rt.drain()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e6)
+        res[label + "_ns_per_hop"] = best / hops
+    mp = rt.model_params()
+    res["f_sm_hz"] = mp.f_sm_hz
+    rt.close()
+    with open(out_path, "w") as f:
+        json.dump(res, f, indent=1)
+    print(res)
+
+
+def _read_ncu_csv(path):
+    """Rows of an ncu --page raw --csv log; each value carries its unit row
+    entry under '<metric>_unit'."""
+    import csv
+    rows = list(csv.reader(open(path)))
+    hdr, units = None, None
+    out = []
+    for r in rows:
+        if "Kernel Name" in r and "ID" in r:
+            hdr = r
+            units = None
+            continue
+        if hdr is None or len(r) != len(hdr):
+            continue
+        if not r[0].strip().isdigit():
+            units = r
+            continue
+        d = dict(zip(hdr, r))
+        if units:
+            d.update({h + "_unit": u for h, u in zip(hdr, units)})
+        out.append(d)
+    return out
+
+
+def _num(x):
+    try:
+        return float(str(x).replace(",", ""))
+    except ValueError:
+        return 0.0
+
+
+def ingest(csv_path, latency_json, out_path, hbm_gbs=None, n_sm=None):
+    """ncu counters (one launch per tenant type, all stages) -> profiles JSON."""
+    import json
+    from paper_1303_5164_gb300 import build, kernelet as K
+    build.build()
+    lat = json.load(open(latency_json))
+    f = lat["f_sm_hz"]
+    rows = _read_ncu_csv(csv_path)
+    agg = {}
+    for r in rows:
+        kname = r.get("Kernel Name", "")
+        key = next((v for k, v in TYPE_OF_KERNEL.items() if k in kname.replace(" ", "")), None)
+        if key is None:
+            continue
+        a = agg.setdefault(key, {"inst": 0, "ld": 0, "req": 0, "sec": 0, "dur_ns": 0, "cyc": 0,
+                                 "dram": 0, "blocks": 0, "warps_x_cyc": 0, "launches": 0})
+        a["inst"] += _num(r["smsp__inst_executed.sum"])
+        a["ld"] += _num(r["smsp__inst_executed_op_global_ld.sum"]) + _num(r["smsp__inst_executed_op_ldgsts.sum"])
+        a["req"] += _num(r["l1tex__t_requests_pipe_lsu_mem_global_op_ld.sum"])
+        a["sec"] += _num(r["l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum"])
+        dur = _num(r["gpu__time_duration.sum"])
+        unit = r.get("gpu__time_duration.sum_unit", "ns")
+        a["dur_ns"] += dur * {"ns": 1, "nsecond": 1, "us": 1e3, "usecond": 1e3, "ms": 1e6,
+                              "msecond": 1e6}.get(unit, 1)
+        cyc = _num(r["sm__cycles_elapsed.avg"])
+        a["cyc"] += cyc
+        a["dram"] += _num(r["dram__bytes_read.sum"]) + _num(r["dram__bytes_write.sum"])
+        a["blocks"] += _num(r["launch__grid_size"])
+        a["warps_x_cyc"] += _num(r["sm__warps_active.avg.per_cycle_active"]) * cyc
+        a["launches"] += 1
+    mp = K.kl_model_params()
+    nsm = n_sm or 152
+    hbm = (hbm_gbs or 6753.1) * 1e9
+    mp.n_sm, mp.n_sched, mp.f_sm_hz, mp.dram_bytes_per_s, mp.sector_bytes, mp.a0, mp.b0 = nsm, 4, f, hbm, 32.0, 1.0, 0.0
+    types = {}
+    for name, a in agg.items():
+        m = a["sec"] / a["req"] if a["req"] else 4.0
+        fu = min(1.0, max(0.0, (m - 4.0) / 28.0))
+        L0_ns = lat["l2_ns_per_hop"] if name in L2_RESIDENT else lat["dram_ns_per_hop"]
+        ipc_meas = a["inst"] / (a["cyc"] * nsm) if a["cyc"] else 0.0
+        w_sm = a["warps_x_cyc"] / a["cyc"] if a["cyc"] else 8.0
+        types[name] = dict(
+            R_m=a["ld"] / a["inst"], f_u=fu, m_c=4.0, m_u=32.0, L0=L0_ns * 1e-9 * f,
+            I_block=a["inst"] / a["blocks"], PUR=a["inst"] / (a["cyc"] * nsm * 4.0),
+            MUR=a["dram"] / (a["dur_ns"] * 1e-9 * hbm), warps_per_block=8,
+            ipc_measured=ipc_meas, warps_per_sm=w_sm, sectors_per_request=m, launches=a["launches"],
+            time_us=a["dur_ns"] / 1e3)
+
+    def predict(a0, b0):
+        mp.a0, mp.b0 = a0, b0
+        err = {}
+        for name, t in types.items():
+            p = K.kl_profile()
+            for k in ("R_m", "f_u", "m_c", "m_u", "L0", "I_block", "PUR", "MUR"):
+                setattr(p, k, t[k])
+            p.warps_per_block, p.valid = 8, 1
+            W = max(1, int(round(t["warps_per_sm"] / 4.0)))
+            W = min(W, 16)
+            err[name] = K.model_ipc(mp, [p], [W], 3)[0]
+        return err
+
+    best = None
+    for a0 in (0.125, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0):
+        for b0 in (0.0, 100.0, 200.0, 400.0, 800.0):
+            pred = predict(a0, b0)
+            sse = sum((pred[n] - types[n]["ipc_measured"]) ** 2 for n in types)
+            if best is None or sse < best[0]:
+                best = (sse, a0, b0, pred)
+    _, a0, b0, pred = best
+    for n in types:
+        types[n]["ipc_predicted"] = pred[n]
+    mae = sum(abs(pred[n] - types[n]["ipc_measured"]) for n in types) / max(1, len(types))
+    out = {"source": f"ncu counters on GB300 ({os.path.basename(csv_path)}), latency probe",
+           "n_sm": nsm, "f_sm_hz": f, "dram_bytes_per_s": hbm, "a0": a0, "b0": b0,
+           "ipc_mae_per_sm": mae, "ipc_peak_per_sm": 4.0, "latency": lat, "types": types}
+    with open(out_path, "w") as fh:
+        json.dump(out, fh, indent=1, sort_keys=True)
+    print(json.dumps({"a0": a0, "b0": b0, "ipc_mae_per_sm": mae,
+                      "per_type": {n: (round(types[n]["ipc_measured"], 3), round(pred[n], 3)) for n in types}}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--types", default="gemm_f32,spmv_csr,blackscholes,pchase,triad,hist256,escape,bitonic")
-    ap.add_argument("--mode", default="native", choices=["native", "cosched"])
+    ap.add_argument("--mode", default="native", choices=["native", "cosched", "mix"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--latency", default=None, help="run the latency probe, write JSON here")
+    ap.add_argument("--ingest", default=None, help="ncu CSV (raw page) to turn into profiles")
+    ap.add_argument("--latency-json", default=None)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--hbm-gbs", type=float, default=None)
     args = ap.parse_args(argv)
+    if args.latency:
+        return latency_probe(args.latency)
+    if args.ingest:
+        return ingest(args.ingest, args.latency_json, args.out, args.hbm_gbs)
     from workloads import gen
     types = args.types.split(",")
     inputs = [gen.gen_tenant(t, 5, i, **scaled_sizes(t, args.scale)) for i, t in enumerate(types)]
@@ -66,13 +246,22 @@ def main(argv=None):
         if rc != 0:
             raise RuntimeError(f"{t.name}: {K.lib().kl_strerror(rc).decode()}")
 
-    for t in tens:          # warm-up pass (not of interest to the profiler: use -s)
-        run(t)
-    torch.cuda.synchronize()
-    for _ in range(args.reps):
+    def run_mix():
         for t in tens:
-            run(t)
-    torch.cuda.synchronize()
+            rt.submit(t.type, t.args)
+        rt.launch()
+        rc = rt.drain()
+        if rc != 0:
+            raise RuntimeError(f"mix: {K.lib().kl_strerror(rc).decode()}")
+
+    # a warm-up pass first (skip it in the profiler with -s)
+    for r in range(1 + args.reps):
+        if args.mode == "mix":
+            run_mix()
+        else:
+            for t in tens:
+                run(t)
+        torch.cuda.synchronize()
     rt.close()
     print("profiled:", ",".join(types), args.mode)
 
