@@ -2,10 +2,12 @@
 within p% (default 2%) of the unsliced execution.
 
 On this runtime a slice is the block range one persistent CTA pulls with one
-atomic; the unsliced reference T_ns is the kernel alone in the co-scheduler
-with one slice per CTA and stage (the fewest pulls that still use every slot).
-For each type, T_s is measured for slices of 1, 2, 4, ... blocks; the chosen
-size is the smallest with T_s / T_ns - 1 <= p (else the fastest measured).
+atomic. For each type the kernel runs alone in the co-scheduler with slices of
+1, 2, 4, ... blocks and with one slice per CTA and stage (the fewest pulls
+that still use every slot). The paper's reference is the unsliced run and
+assumes the overhead falls as slices grow; here it does not always (very
+large slices unbalance the SMs), so T_ns is the fastest of the measured runs,
+and the chosen size is the smallest with T_s / T_ns - 1 <= p.
 
     python -m paper_1303_5164_gb300.autotune --out slices.json [--p 0.02]
 """
@@ -49,9 +51,8 @@ def tune(types, p=0.02, reps=3, seed=6):
             return best
 
         times = {c: run(c) for c in cands}
-        tns = times[ref]
-        ok = [c for c in cands if times[c] / tns - 1.0 <= p]
-        chosen = min(ok) if ok else min(times, key=times.get)
+        tns = min(times.values())
+        chosen = min(c for c in cands if times[c] / tns - 1.0 <= p)
         out["slices"][ty] = chosen
         out["times_us"][ty] = {str(c): round(v, 2) for c, v in times.items()}
         out["overhead"][ty] = round(times[chosen] / tns - 1.0, 4)
