@@ -103,7 +103,7 @@ typedef struct {            /* KL_T_BLACKSCHOLES: 256 options per block       */
     uint64_t n;
 } kl_args_blackscholes;
 
-typedef struct {            /* KL_T_GEMM_F32: one 128x64 tile of C per block  */
+typedef struct {            /* KL_T_GEMM_F32: one 64x64 tile of C per block   */
     const float* A;         /* [M][K] 16B                                      */
     const float* B;         /* [K][N] 16B                                      */
     float* C;               /* [M][N] 16B                                      */
@@ -201,6 +201,9 @@ typedef enum {
                                can use (stage barrier, spread rule, re-plan in
                                flight) runs a slice of another pending kernel;
                                default on */
+#define KL_CFG_FILL_TYPES 2u /* backfill tries the next pending kernels of the two
+                               types the co-schedule runs before any other
+                               pending kernel; default on */
 
 typedef struct {
     int32_t device;                 /* CUDA ordinal (default 0)                     */

@@ -48,6 +48,9 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Co-resident CTAs per SM: 4 x 256 threads at up to 64 registers each.
+constexpr int kCtasPerSm = 4;
+
 enum : uint32_t { kActRun = 0, kActWait = 1, kActExit = 2, kActReplan = 3 };
 enum : int { kPulled = 0, kBlocked = 1, kExhausted = 2 };
 
@@ -179,9 +182,24 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
       }
     }
   }
+  // backfill candidates: the next pending kernel of A's type and of B's type
+  // (more of the work the pair is doing), then the lowest pending indices
   for (int f = 0; f < 4; ++f) ph.fill[f] = -1;
-  for (uint32_t f = 0, c = 0; f < nlow && c < 4; ++f)
-    if (lowp[f] != ph.A && lowp[f] != ph.B) ph.fill[c++] = lowp[f];
+  uint32_t c = 0;
+  if (ph.A >= 0 && (R->flags & KL_CFG_FILL_TYPES)) {
+    const uint32_t ta = T[ph.A].type;
+    const int32_t sa = low1[ta] != ph.A ? low1[ta] : low2[ta];
+    if (sa >= 0 && sa != ph.B) ph.fill[c++] = sa;
+    if (ph.B >= 0) {
+      const uint32_t tb = T[ph.B].type;
+      const int32_t sb = low1[tb] != ph.B ? low1[tb] : low2[tb];
+      if (sb >= 0 && sb != ph.A && (c == 0 || sb != ph.fill[0])) ph.fill[c++] = sb;
+    }
+  }
+  for (uint32_t f = 0; f < nlow && c < 4; ++f)
+    if (lowp[f] != ph.A && lowp[f] != ph.B && (c == 0 || lowp[f] != ph.fill[0]) &&
+        (c < 2 || lowp[f] != ph.fill[1]))
+      ph.fill[c++] = lowp[f];
   const uint32_t seq = seq_old + 1;
   if (seq >= R->max_phases) {
     set_error(R, KL_EOVERFLOW, seq);
@@ -203,7 +221,7 @@ __device__ __forceinline__ void complete_tenant(TenantDev& d, RunDev* R) {
   atomicMax(&R->t_end, now);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) cosched_kernel(TenantDev* __restrict__ T, RunDev* __restrict__ R,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev* __restrict__ T, RunDev* __restrict__ R,
                                                              PhaseDev* __restrict__ P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaCtl ctl;

@@ -416,7 +416,7 @@ extern "C" int kl_config_default(kl_config* c) {
   c->mem_cap_bytes = 0;
   c->alpha_p = -1.0;
   c->alpha_m = -1.0;
-  c->flags = KL_CFG_BACKFILL;
+  c->flags = KL_CFG_BACKFILL | KL_CFG_FILL_TYPES;
   return KL_OK;
 }
 

@@ -39,7 +39,8 @@ __host__ __device__ inline uint32_t cdiv64(uint64_t a, uint64_t b) {
 
 constexpr int kGatherPerBlock = 1024;
 constexpr int kBsPerBlock = 256;
-constexpr int kGemmBM = 128, kGemmBN = 64, kGemmBK = 16;
+constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 16;
+constexpr int kGemmAStride = kGemmBM + 4;  // k-major A tile row (16-byte aligned, fewer bank conflicts)
 constexpr int kSpmvRowsPerBlock = 32;
 constexpr int kSpmvLanesPerRow = 8;
 constexpr int kChasersPerBlock = 256;
@@ -119,7 +120,7 @@ __host__ __device__ inline Stage stage_of(uint32_t type, const void* a, uint32_t
 
 __host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
   switch (type) {
-    case KL_T_GEMM_F32: return 2u * (kGemmBM * kGemmBK + kGemmBK * kGemmBN) * 4u;  // 24 KB
+    case KL_T_GEMM_F32: return 2u * (kGemmBK * kGemmAStride + kGemmBK * kGemmBN) * 4u;  // 16.5 KB
     case KL_T_SPMV_CSR: return 256u;                                              // long-row list
     case KL_T_HIST256: return 256u * 32u * 4u;                                    // 32 KB
     case KL_T_BITONIC: return ((1u << kBitonicTileLog2) + (1u << (kBitonicTileLog2 - 5))) * 4u;  // padded tile
@@ -127,6 +128,7 @@ __host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
   }
 }
 constexpr uint32_t kMaxTenantSmem = 256u * 32u * 4u;  // largest of the above (histogram)
+static_assert(2u * (kGemmBK * kGemmAStride + kGemmBK * kGemmBN) * 4u <= kMaxTenantSmem, "smem bound");
 
 #ifdef __CUDACC__
 
@@ -281,93 +283,91 @@ __device__ __forceinline__ void blackscholes_block(const kl_args_blackscholes& a
 }
 
 // ------------------------------------------------------------------ FP32 GEMM
-// 128x64 tile of C per block; 256 threads as 16x16, each an 8x4 micro-tile
-// (rows ty*8..+7, cols tx*4..+3). K advances in 16-wide tiles staged in shared
-// memory by cp.async (double buffered, zero-filled past the edges). For every
+// 64x64 tile of C per block; 256 threads as 16x16, each a 4x4 micro-tile (rows
+// ty*4..+3, cols tx*4..+3). K advances in 16-wide tiles: B by cp.async into a
+// [k][n] shared tile, A through registers into a k-major [k][m] shared tile,
+// both double buffered and zero-filled past the edges. Each k step is one
+// 128-bit shared load of A and one of B for 16 fused multiply-adds. For every
 // C[i][j] the fused multiply-adds run over k = 0,1,2,... in order from +0, so
 // the result is the ascending fused chain exactly (zero padding adds exact 0).
 
 __device__ __forceinline__ void gemm_f32_block(const kl_args_gemm_f32& a, uint32_t vb, char* smem) {
-  float* As = reinterpret_cast<float*>(smem);            // [2][128][16]
-  float* Bs = As + 2 * kGemmBM * kGemmBK;                 // [2][16][64]
+  float* As = reinterpret_cast<float*>(smem);            // [2][16][68]  (k-major)
+  float* Bs = As + 2 * kGemmBK * kGemmAStride;            // [2][16][64]
   const uint32_t tilesN = (a.N + kGemmBN - 1) / kGemmBN;
   const uint32_t m0 = (vb / tilesN) * kGemmBM;
   const uint32_t n0 = (vb % tilesN) * kGemmBN;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const uint32_t ktiles = (a.K + kGemmBK - 1) / kGemmBK;
+  // A loader: row m = tid % 64 of the tile, k chunk (tid / 64) * 4; it walks
+  // a precomputed pointer so the argument block need not stay in registers
+  const uint32_t akc = (tid >> 6) * 4;
+  const bool arow_ok = m0 + (tid & 63) < a.M;
+  const float* aptr = a.A + (uint64_t)(arow_ok ? m0 + (tid & 63) : 0) * a.K + akc;
+  const uint32_t K = a.K;
 
-  auto load_tile = [&](uint32_t kt, int buf) {
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      int c = tid + u * 256;
-      int row = c >> 2, kc = c & 3;
-      uint32_t gm = m0 + row, gk = kt * kGemmBK + kc * 4;
-      bool ok = gm < a.M && gk < a.K;
-      const float* src = ok ? a.A + (uint64_t)gm * a.K + gk : a.A;
-      cp_async16(As + buf * kGemmBM * kGemmBK + row * kGemmBK + kc * 4, src, ok ? 16 : 0);
-    }
-    {
-      int row = tid >> 4, nc = tid & 15;
-      uint32_t gk = kt * kGemmBK + row, gn = n0 + nc * 4;
-      bool ok = gk < a.K && gn < a.N;
-      const float* src = ok ? a.B + (uint64_t)gk * a.N + gn : a.B;
-      cp_async16(Bs + buf * kGemmBK * kGemmBN + row * kGemmBN + nc * 4, src, ok ? 16 : 0);
-    }
+  auto load_a = [&](uint32_t kt) -> float4 {
+    const uint32_t gk = kt * kGemmBK + akc;
+    if (arow_ok && gk < K) return __ldg(reinterpret_cast<const float4*>(aptr + kt * kGemmBK));
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto store_a = [&](float4 v, int buf) {
+    float* d = As + buf * kGemmBK * kGemmAStride + akc * kGemmAStride + (tid & 63);
+    d[0] = v.x;
+    d[kGemmAStride] = v.y;
+    d[2 * kGemmAStride] = v.z;
+    d[3 * kGemmAStride] = v.w;
+  };
+  auto load_b = [&](uint32_t kt, int buf) {
+    const int row = tid >> 4, nc = tid & 15;
+    const uint32_t gk = kt * kGemmBK + row, gn = n0 + nc * 4;
+    const bool ok = gk < a.K && gn < a.N;
+    const float* src = ok ? a.B + (uint64_t)gk * a.N + gn : a.B;
+    cp_async16(Bs + buf * kGemmBK * kGemmBN + row * kGemmBN + nc * 4, src, ok ? 16 : 0);
     cp_async_commit();
   };
 
-  float acc[8][4];
+  float acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
 
-  load_tile(0, 0);
+  store_a(load_a(0), 0);
+  load_b(0, 0);
   for (uint32_t kt = 0; kt < ktiles; ++kt) {
+    const int buf = kt & 1;
+    float4 an = make_float4(0.f, 0.f, 0.f, 0.f);
     if (kt + 1 < ktiles) {
-      load_tile(kt + 1, (kt + 1) & 1);
+      an = load_a(kt + 1);  // lands in registers while this tile is computed
+      load_b(kt + 1, buf ^ 1);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float* Ab = As + (kt & 1) * kGemmBM * kGemmBK + ty * 8 * kGemmBK;
-    const float* Bb = Bs + (kt & 1) * kGemmBK * kGemmBN + tx * 4;
+    const float* Ab = As + buf * kGemmBK * kGemmAStride + ty * 4;
+    const float* Bb = Bs + buf * kGemmBK * kGemmBN + tx * 4;
 #pragma unroll
-    for (int k4 = 0; k4 < kGemmBK / 4; ++k4) {
-      float4 b0 = *reinterpret_cast<const float4*>(Bb + (k4 * 4 + 0) * kGemmBN);
-      float4 b1 = *reinterpret_cast<const float4*>(Bb + (k4 * 4 + 1) * kGemmBN);
-      float4 b2 = *reinterpret_cast<const float4*>(Bb + (k4 * 4 + 2) * kGemmBN);
-      float4 b3 = *reinterpret_cast<const float4*>(Bb + (k4 * 4 + 3) * kGemmBN);
+    for (int k = 0; k < kGemmBK; ++k) {
+      const float4 av = *reinterpret_cast<const float4*>(Ab + k * kGemmAStride);
+      const float4 bv = *reinterpret_cast<const float4*>(Bb + k * kGemmBN);
+      const float ar[4] = {av.x, av.y, av.z, av.w};
+      const float br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float4 av = *reinterpret_cast<const float4*>(Ab + i * kGemmBK + k4 * 4);
-        acc[i][0] = __fmaf_rn(av.x, b0.x, acc[i][0]);
-        acc[i][1] = __fmaf_rn(av.x, b0.y, acc[i][1]);
-        acc[i][2] = __fmaf_rn(av.x, b0.z, acc[i][2]);
-        acc[i][3] = __fmaf_rn(av.x, b0.w, acc[i][3]);
-        acc[i][0] = __fmaf_rn(av.y, b1.x, acc[i][0]);
-        acc[i][1] = __fmaf_rn(av.y, b1.y, acc[i][1]);
-        acc[i][2] = __fmaf_rn(av.y, b1.z, acc[i][2]);
-        acc[i][3] = __fmaf_rn(av.y, b1.w, acc[i][3]);
-        acc[i][0] = __fmaf_rn(av.z, b2.x, acc[i][0]);
-        acc[i][1] = __fmaf_rn(av.z, b2.y, acc[i][1]);
-        acc[i][2] = __fmaf_rn(av.z, b2.z, acc[i][2]);
-        acc[i][3] = __fmaf_rn(av.z, b2.w, acc[i][3]);
-        acc[i][0] = __fmaf_rn(av.w, b3.x, acc[i][0]);
-        acc[i][1] = __fmaf_rn(av.w, b3.y, acc[i][1]);
-        acc[i][2] = __fmaf_rn(av.w, b3.z, acc[i][2]);
-        acc[i][3] = __fmaf_rn(av.w, b3.w, acc[i][3]);
-      }
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(ar[i], br[j], acc[i][j]);
     }
+    if (kt + 1 < ktiles) store_a(an, buf ^ 1);
     __syncthreads();
   }
   const uint32_t gn = n0 + tx * 4;
   if (gn < a.N) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      uint32_t gm = m0 + ty * 8 + i;
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t gm = m0 + ty * 4 + i;
       if (gm < a.M)
         *reinterpret_cast<float4*>(a.C + (uint64_t)gm * a.N + gn) =
             make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
@@ -454,6 +454,8 @@ __device__ __forceinline__ void spmv_csr_block(const kl_args_spmv_csr& a, uint32
 // ------------------------------------------------------------------ pointer chase
 
 __device__ __forceinline__ void pchase_block(const kl_args_pchase& a, uint32_t vb) {
+  // one chain per thread: the chains of a kernel spread over every SM, whose
+  // outstanding-miss capacity bounds how many dependent loads are in flight
   const uint32_t t = vb * kChasersPerBlock + threadIdx.x;
   if (t >= a.nchasers) return;
   int p = __ldg(a.start + t);
@@ -609,13 +611,13 @@ template <int M>
 __device__ __forceinline__ void bitonic_fused(uint32_t* out, uint32_t vb, uint32_t lv, uint32_t jlo) {
   constexpr int G = 1 << M;                 // keys per group
   constexpr int PER_THREAD = 16 / G;        // groups per thread (16 keys per thread)
-  const uint64_t k = 1ull << lv;
-  const uint64_t s = 1ull << jlo;
-  uint64_t base[PER_THREAD];
+  const uint32_t k = 1u << lv;              // keys < 2^30: 32-bit indices throughout
+  const uint32_t s = 1u << jlo;
+  uint32_t base[PER_THREAD];
   uint32_t v[16];
 #pragma unroll
   for (int u = 0; u < PER_THREAD; ++u) {
-    const uint64_t q = (uint64_t)vb * (4096 / G) + (uint64_t)u * 256 + threadIdx.x;
+    const uint32_t q = vb * (4096u / G) + (uint32_t)u * 256u + threadIdx.x;
     base[u] = ((q >> jlo) << (jlo + M)) | (q & (s - 1));
 #pragma unroll
     for (int r = 0; r < G; ++r) v[u * G + r] = __ldcg(out + base[u] + r * s);
@@ -709,7 +711,7 @@ __device__ __forceinline__ void bt_store(const uint32_t (&v)[16], uint32_t* t) {
 // Levels with register-index bits bhi..blo (descending) at merge size k;
 // direction from the global index of each pair.
 template <int PAT>
-__device__ __forceinline__ void bt_levels(uint32_t (&v)[16], int bhi, int blo, uint64_t k, uint64_t gbase) {
+__device__ __forceinline__ void bt_levels(uint32_t (&v)[16], int bhi, int blo, uint32_t k, uint32_t gbase) {
 #pragma unroll
   for (int b = 3; b >= 0; --b) {
     if (b > bhi || b < blo) continue;
@@ -737,7 +739,7 @@ __device__ __forceinline__ void bt_levels_dir(uint32_t (&v)[16]) {
 }
 
 // Tile merge for k > 4096: all 12 distances 2048 .. 1, direction uniform.
-__device__ __forceinline__ void bitonic_tile_merge_regs(uint32_t* out, uint32_t* t, uint64_t gbase, uint64_t k) {
+__device__ __forceinline__ void bitonic_tile_merge_regs(uint32_t* out, uint32_t* t, uint32_t gbase, uint32_t k) {
   const bool asc = (gbase & k) == 0;
   uint32_t v[16];
 #pragma unroll
@@ -758,7 +760,7 @@ __device__ __forceinline__ void bitonic_tile_merge_regs(uint32_t* out, uint32_t*
 
 // Full sort of a 4096-key tile (merge sizes 2 .. 4096), keys read from `in`.
 __device__ __forceinline__ void bitonic_tile_sort_regs(const uint32_t* in, uint32_t* out, uint32_t* t,
-                                                       uint64_t gbase) {
+                                                       uint32_t gbase) {
   uint32_t v[16];
   const uint4* src = reinterpret_cast<const uint4*>(in + gbase + 16u * threadIdx.x);
 #pragma unroll
@@ -771,10 +773,10 @@ __device__ __forceinline__ void bitonic_tile_sort_regs(const uint32_t* in, uint3
   }
   // k = 2, 4, 8, 16 inside the thread's 16 consecutive keys
 #pragma unroll
-  for (int lv = 1; lv <= 4; ++lv) bt_levels<2>(v, lv - 1, 0, 1ull << lv, gbase);
+  for (int lv = 1; lv <= 4; ++lv) bt_levels<2>(v, lv - 1, 0, 1u << lv, gbase);
   int pat = 2;  // pattern the registers currently follow
   for (uint32_t lv = 5; lv <= 12; ++lv) {
-    const uint64_t k = 1ull << lv;
+    const uint32_t k = 1u << lv;
     if (lv >= 9) {  // distances 2^(lv-1) .. 256
       bt_store<2>(v, t);
       __syncthreads();
@@ -815,12 +817,12 @@ __device__ __forceinline__ void bitonic_block(const kl_args_bitonic& a, uint32_t
     return;
   }
   uint32_t* t = reinterpret_cast<uint32_t*>(smem);
-  const uint64_t gbase = (uint64_t)vb * tile_n;
+  const uint32_t gbase = vb * tile_n;
   if (tile_n == 4096u) {
     if (st.kind == 0)
       bitonic_tile_sort_regs(a.in, a.out, t, gbase);
     else
-      bitonic_tile_merge_regs(a.out, t, gbase, 1ull << st.lv);
+      bitonic_tile_merge_regs(a.out, t, gbase, 1u << st.lv);
     return;
   }
   // small sorts (fewer than 4096 keys): one block, shared-memory network

@@ -28,6 +28,7 @@ TYPE_NAMES = ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad
 KL_RATIO_BALANCED, KL_RATIO_MAX_CP, KL_RATIO_FIXED = 0, 1, 2
 KL_BASE_SERIAL, KL_BASE_MULTISTREAM = 0, 1
 KL_CFG_BACKFILL = 1
+KL_CFG_FILL_TYPES = 2
 
 P = C.c_void_p
 U32, U64, I32, F32, F64 = C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
