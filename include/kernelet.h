@@ -254,6 +254,8 @@ typedef struct {
     int32_t trigger;        /* tenant whose exhaustion ended the previous phase  */
     uint32_t n_pending;     /* kernels with blocks left when the phase was chosen */
     uint64_t pending_mask;  /* bit i: kernel i (i < 64) was pending               */
+    uint32_t done_a, done_b;          /* blocks finished by A, B at publication    */
+    uint32_t prev_done_a, prev_done_b;/* by the previous phase's A, B at that time */
 } kl_phase;
 
 typedef struct {

@@ -108,6 +108,7 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
   unsigned long long pmask = 0ull;
   int32_t lowp[6];
   uint32_t nlow = 0;
+  int32_t lowms = -1;  // lowest pending kernel with more than one stage
   const uint32_t n = R->n_tenants;
   for (uint32_t base = 0; base < n; base += 32) {
     const uint32_t i = base + lane;
@@ -121,6 +122,8 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
     npend += __popc(pb);
     if (base < 64) pmask |= (unsigned long long)pb << base;
     for (uint32_t m = pb; m && nlow < 6; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
+    const uint32_t msb = __ballot_sync(0xffffffffu, pend && T[min(i, n - 1)].nstages > 1);
+    if (msb && lowms < 0) lowms = (int32_t)(base + __ffs(msb) - 1);
 #pragma unroll
     for (int t = 0; t < KL_T_COUNT; ++t) {
       uint32_t m = __ballot_sync(0xffffffffu, pend && ty == (uint32_t)t);
@@ -196,15 +199,30 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
       if (sb >= 0 && sb != ph.A && (c == 0 || sb != ph.fill[0])) ph.fill[c++] = sb;
     }
   }
-  for (uint32_t f = 0; f < nlow && c < 4; ++f)
-    if (lowp[f] != ph.A && lowp[f] != ph.B && (c == 0 || lowp[f] != ph.fill[0]) &&
-        (c < 2 || lowp[f] != ph.fill[1]))
-      ph.fill[c++] = lowp[f];
+  // then the lowest pending multi-stage kernel (a long chain of dependent
+  // grids: started early, its stage barriers overlap other work instead of
+  // forming the tail of the run), then the lowest pending indices
+  if (lowms >= 0 && c < 4 && lowms != ph.A && lowms != ph.B && (c == 0 || lowms != ph.fill[0]) &&
+      (c < 2 || lowms != ph.fill[1]))
+    ph.fill[c++] = lowms;
+  for (uint32_t f = 0; f < nlow && c < 4; ++f) {
+    bool dup = lowp[f] == ph.A || lowp[f] == ph.B;
+    for (uint32_t q = 0; q < c; ++q) dup |= lowp[f] == ph.fill[q];
+    if (!dup) ph.fill[c++] = lowp[f];
+  }
   const uint32_t seq = seq_old + 1;
   if (seq >= R->max_phases) {
     set_error(R, KL_EOVERFLOW, seq);
     ph.A = -1;
     ph.B = -1;
+  }
+  // block counts at this instant: per-phase measured progress of each kernel
+  ph.done_a = ph.A >= 0 ? ld_relaxed(&T[ph.A].done) : 0u;
+  ph.done_b = ph.B >= 0 ? ld_relaxed(&T[ph.B].done) : 0u;
+  {
+    const int32_t pa = __ldcg(&P[seq_old].A), pb = __ldcg(&P[seq_old].B);
+    ph.prev_done_a = pa >= 0 ? ld_relaxed(&T[pa].done) : 0u;
+    ph.prev_done_b = pb >= 0 ? ld_relaxed(&T[pb].done) : 0u;
   }
   ph.t = gtimer();
   P[min(seq, R->max_phases - 1)] = ph;

@@ -43,8 +43,11 @@ struct PhaseDev {
   uint32_t n_pending;          // kernels with blocks left when the phase was chosen
   unsigned long long pending;  // bit i: kernel i (i < 64) was pending
   int32_t fill[4];             // other pending kernels (lowest indices) for backfill
+  uint32_t done_a, done_b;     // blocks finished by this phase's A, B when it was published
+  uint32_t prev_done_a;        // ... and by the previous phase's A, B at the same moment
+  uint32_t prev_done_b;
 };
-static_assert(sizeof(PhaseDev) == 64, "PhaseDev layout");
+static_assert(sizeof(PhaseDev) == 80, "PhaseDev layout");
 
 // Run-wide state of one co-scheduled launch.
 struct alignas(128) RunDev {

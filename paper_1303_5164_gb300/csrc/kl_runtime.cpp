@@ -299,6 +299,10 @@ int retire(kl_runtime* rt) {
       q.trigger = p.trigger;
       q.n_pending = p.n_pending;
       q.pending_mask = p.pending;
+      q.done_a = p.done_a;
+      q.done_b = p.done_b;
+      q.prev_done_a = p.prev_done_a;
+      q.prev_done_b = p.prev_done_b;
       rt->last_phases.push_back(q);
     }
     for (uint32_t i = 0; i < n; ++i) {

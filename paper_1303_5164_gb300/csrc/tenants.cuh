@@ -709,16 +709,23 @@ __device__ __forceinline__ void bt_store(const uint32_t (&v)[16], uint32_t* t) {
 }
 
 // Levels with register-index bits bhi..blo (descending) at merge size k;
-// direction from the global index of each pair.
+// direction from the global index of each pair. The tile index of a pattern is
+// a bit field of (thread bits, register bits), so bit log2(k) of the global
+// index is either a register bit (known per r at compile time) or the same for
+// all of the thread's keys.
 template <int PAT>
 __device__ __forceinline__ void bt_levels(uint32_t (&v)[16], int bhi, int blo, uint32_t k, uint32_t gbase) {
+  constexpr uint32_t r_lo = PAT == 0 ? 8u : (PAT == 1 ? 4u : 0u);  // lowest tile bit taken from r
+  const uint32_t lk = 31u - __clz(k);
+  const uint32_t rmask = (lk >= r_lo && lk < r_lo + 4u) ? 1u << (lk - r_lo) : 0u;
+  const bool tasc = ((gbase + bt_elem<PAT>(threadIdx.x, 0)) & k) == 0;
 #pragma unroll
   for (int b = 3; b >= 0; --b) {
     if (b > bhi || b < blo) continue;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       if (r & (1 << b)) continue;
-      const bool asc = ((gbase + bt_elem<PAT>(threadIdx.x, r)) & k) == 0;
+      const bool asc = rmask ? ((uint32_t)r & rmask) == 0 : tasc;
       cmpx(v[r], v[r | (1 << b)], asc);
     }
   }

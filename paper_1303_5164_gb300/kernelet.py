@@ -112,7 +112,8 @@ class kl_model_params(C.Structure):
 
 class kl_phase(C.Structure):
     _fields_ = [("A", I32), ("B", I32), ("slots_a", U32), ("slots_b", U32), ("cp", F64),
-                ("t_ns", U64), ("trigger", I32), ("n_pending", U32), ("pending_mask", U64)]
+                ("t_ns", U64), ("trigger", I32), ("n_pending", U32), ("pending_mask", U64),
+                ("done_a", U32), ("done_b", U32), ("prev_done_a", U32), ("prev_done_b", U32)]
 
 
 class kl_tenant_stats(C.Structure):

@@ -1,0 +1,180 @@
+"""Markov model vs measured co-scheduled IPC on the GPU (Section 5.3:
+single-kernel and concurrent-kernel IPC prediction, CP prediction).
+
+Every kernel type runs alone in the co-scheduler, then every pair of types
+runs co-scheduled at the model's balanced slot split (Eq. executiontime). The
+measured IPC of a kernel in a phase is its blocks finished during the phase
+(from the phase log) times its instructions per block (measured with ncu)
+over the phase's cycles on all SMs. The model's numbers come from the
+runtime's own model with the measured per-type profiles.
+
+The two-tenant case (Black-Scholes 65,536 options + int32 gather 2^20, each
+in 4 slices) is also run at fixed slot ratios 1:3, 1:1 and 3:1 and against
+the same two kernels as plain launches on 2 streams.
+
+    python -m paper_1303_5164_gb300.validate_pairs --out pairs.json
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import os
+import statistics
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+TYPES = ["gemm_f32", "spmv_csr", "blackscholes", "pchase", "triad", "hist256", "escape", "bitonic"]
+
+
+def _profiles(K):
+    path = os.path.join(ROOT, "paper_1303_5164_gb300", "profiles_gb300.json")
+    with open(path) as f:
+        doc = json.load(f)
+    profs = []
+    for name in K.TYPE_NAMES:
+        p = K.kl_profile()
+        e = doc["types"].get(name)
+        if e:
+            for k in ("R_m", "f_u", "m_c", "m_u", "L0", "I_block", "PUR", "MUR"):
+                setattr(p, k, float(e[k]))
+            p.warps_per_block = 8
+            p.slice_blocks = int(doc.get("slices", {}).get(name, 0))
+            p.valid = 1
+        profs.append(p)
+    return profs, doc
+
+
+def _phase_ipc(ph, i, tens, profs, mp):
+    """Measured per-SM IPC of the kernels of phase i (ends at phase i+1)."""
+    p, q = ph[i], ph[i + 1]
+    cycles = (q.t_ns - p.t_ns) * 1e-9 * mp.f_sm_hz
+    out = []
+    for who, d0, d1 in ((p.A, p.done_a, q.prev_done_a), (p.B, p.done_b, q.prev_done_b)):
+        if who < 0:
+            out.append(None)
+            continue
+        ib = profs[tens[who].type].I_block
+        out.append((d1 - d0) * ib / (cycles * mp.n_sm) if cycles > 0 else None)
+    return out, (q.t_ns - p.t_ns) / 1e3
+
+
+def run(out_path, reps=3):
+    import torch
+    from workloads import gen
+    from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
+    build.build()
+    profs, doc = _profiles(K)
+    cfg = K.config_default()
+    cfg.slots_per_sm = 4
+    rt = K.Runtime(cfg)
+    mp = rt.model_params()
+    mp.a0, mp.b0 = doc.get("a0", 1.0), doc.get("b0", 0.0)
+    mp.dram_bytes_per_s = doc.get("dram_bytes_per_s", mp.dram_bytes_per_s)
+    rt.set_model_params(mp)
+    rt.set_profiles(profs)
+    S = rt.run_stats().slots_per_sm
+    tens = {t: T.make(t, gen.gen_tenant(t, 9, i, **T.SIZES_MIX[t])) for i, t in enumerate(TYPES)}
+    res = {"slots_per_sm": S, "f_sm_hz": mp.f_sm_hz, "n_sm": mp.n_sm, "solo": {}, "pairs": {}}
+
+    def go(names, policy=K.KL_RATIO_BALANCED, fixed=2, slices=None):
+        c2 = K.config_default()
+        c2.slots_per_sm = S
+        c2.ratio_policy = policy
+        c2.fixed_slots_a = fixed
+        r2 = K.Runtime(c2)
+        r2.set_model_params(mp)
+        r2.set_profiles(profs)
+        best = None
+        for _ in range(reps):
+            for j, nm in enumerate(names):
+                r2.submit(tens[nm].type, tens[nm].args, slice_blocks=(slices[j] if slices else 0))
+            r2.launch()
+            assert r2.drain() == 0
+            ph = r2.phases()
+            ker = r2.run_stats().kernel_ns / 1e3
+            if best is None or ker < best[1]:
+                best = (ph, ker)
+        r2.close()
+        return best
+
+    # solo IPC of each type at the co-scheduler's full occupancy
+    for nm in TYPES:
+        ph, ker = go([nm])
+        (ipc, _), dur = _phase_ipc(ph, 1, [tens[nm]], profs, mp)
+        w = max(1, int(round(S * 8 / 4)))
+        pred = K.model_ipc(mp, [profs[tens[nm].type]], [w], 3)[0]
+        res["solo"][nm] = {"ipc_measured": ipc, "ipc_predicted": pred, "phase_us": dur, "kernel_us": ker}
+        print("solo", nm, res["solo"][nm], flush=True)
+
+    # all pairs at the model's balanced split
+    for a, b in itertools.combinations(TYPES, 2):
+        ph, ker = go([a, b])
+        (ca, cb), dur = _phase_ipc(ph, 1, [tens[a], tens[b]], profs, mp)
+        sa = ph[1].slots_a
+        pr = K.model_pair(mp, profs[tens[a].type], profs[tens[b].type], S, 3)
+        pa, pb = pr["cipc_a"][sa - 1], pr["cipc_b"][sa - 1]
+        ia, ib = res["solo"][a]["ipc_measured"], res["solo"][b]["ipc_measured"]
+        cp_meas = 1.0 - 1.0 / (ca / ia + cb / ib) if ca and cb and ia and ib else None
+        res["pairs"][f"{a}+{b}"] = {
+            "slots_a": sa, "slots_b": S - sa, "cipc_measured": [ca, cb], "cipc_predicted": [pa, pb],
+            "ipc_sum_measured": (ca or 0) + (cb or 0), "ipc_sum_predicted": pa + pb,
+            "cp_predicted": pr["cp"][sa - 1], "cp_measured": cp_meas, "phase_us": dur, "kernel_us": ker}
+        print("pair", a, b, json.dumps(res["pairs"][f"{a}+{b}"]), flush=True)
+
+    # the two-tenant case at fixed ratios, and on two streams
+    bs = T.make("blackscholes", gen.gen_blackscholes(1, 0, 65536))
+    ga = T.make("gather", gen.gen_gather(1, 1, 1 << 20))
+    tens["bs65k"], tens["gather1m"] = bs, ga
+    slices = [bs.shape().total_blocks // 4, ga.shape().total_blocks // 4]
+    c1 = {}
+    for sa in (1, 2, 3):
+        ph, ker = go(["bs65k", "gather1m"], K.KL_RATIO_FIXED, sa, slices)
+        (ca, cb), dur = _phase_ipc(ph, 1, [bs, ga], profs, mp)
+        pr = K.model_pair(mp, profs[bs.type], profs[ga.type], S, 3, K.KL_RATIO_FIXED, sa)
+        c1[f"{sa}:{S - sa}"] = {"kernel_us": ker, "cipc_measured": [ca, cb],
+                                "cipc_predicted": [pr["cipc_a"][sa - 1], pr["cipc_b"][sa - 1]],
+                                "cp_predicted": pr["cp"][sa - 1], "dT_predicted": pr["dT"][sa - 1]}
+        print("c1", sa, c1[f"{sa}:{S - sa}"], flush=True)
+    r2 = K.Runtime()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps + 1):
+        r2.submit(bs.type, bs.args)
+        r2.submit(ga.type, ga.args)
+        torch.cuda.synchronize()
+        e0.record()
+        r2.launch_baseline(K.KL_BASE_MULTISTREAM, 2)
+        r2.drain()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    c1["two_streams_us"] = min(times)
+    res["c1_pair"] = c1
+    r2.close()
+
+    errs = [abs(v["ipc_sum_measured"] - v["ipc_sum_predicted"]) for v in res["pairs"].values()]
+    per = [abs(m - p) for v in res["pairs"].values() for m, p in zip(v["cipc_measured"], v["cipc_predicted"])
+           if m is not None]
+    solo_err = [abs(v["ipc_measured"] - v["ipc_predicted"]) for v in res["solo"].values() if v["ipc_measured"]]
+    res["summary"] = {"pair_ipc_sum_mae_per_sm": statistics.mean(errs), "pair_cipc_mae_per_sm": statistics.mean(per),
+                      "solo_ipc_mae_per_sm": statistics.mean(solo_err), "ipc_peak_per_sm": 4.0,
+                      "pairs_within_20pct_of_peak": sum(e <= 0.8 for e in errs), "pairs": len(errs)}
+    print(json.dumps(res["summary"]))
+    rt.close()
+    with open(out_path, "w") as f:
+        json.dump(res, f, indent=1)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    run(a.out)
+
+
+if __name__ == "__main__":
+    main()
