@@ -33,6 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "kernel-mix throughput (kernels/s) & makespan speedup vs multi-stream on 1 GB300; p99 latency"
+BATCH_WORKLOAD = ("batch of 512 tenants, types uniform over the eight mix kernels, grids log-uniform in "
+                  "[1, 4096] blocks, problem sizes scaled to the grid, one persistent launch")
 WORKLOAD = ("8-tenant mix, 64 kernels (8 each of FP32 GEMM 1024^3, CSR SpMV 1Mi rows power-law mean 16, "
             "Black-Scholes 4Mi, pointer-chase 64MiB x 65536 chasers x 256 hops, triad 64Mi, hist256 64Mi "
             "Zipf(1.1), escape-time 2048^2 max 256, bitonic 2^22), seeded order")
@@ -52,6 +54,38 @@ def mix_jobs(seed: int = 2, copies: int = 8):
     order = [t for t in MIX_TYPES for _ in range(copies)]
     np.random.default_rng(seed).shuffle(order)
     return [(nm, seed, i, SIZES_MIX[nm]) for i, nm in enumerate(order)]
+
+
+def batch_sizes(name: str, g: int) -> dict:
+    """Problem size of a tenant whose (main-stage) grid is g blocks."""
+    if name == "gemm_f32":
+        a = 1 << (g.bit_length() - 1) // 2
+        return dict(M=64 * a, N=64 * -(-g // a), K=512)
+    if name == "spmv_csr":
+        return dict(nrows=32 * g)
+    if name == "blackscholes":
+        return dict(n=256 * g)
+    if name == "pchase":
+        return dict(N=max(1 << 16, 4096 * g), nchasers=256 * g, hops=256)
+    if name == "triad":
+        return dict(n=4096 * g)
+    if name == "hist256":
+        return dict(n=32768 * g)
+    if name == "escape":
+        return dict(width=256, height=g, max_iter=256)
+    if name == "bitonic":
+        return dict(log2n=12 + g.bit_length() - 1)
+    raise ValueError(name)
+
+
+def batch_jobs(seed: int = 3, n: int = 512):
+    """512 tenants: types uniform over the eight, grids log-uniform in [1, 4096]."""
+    import numpy as np
+    from paper_1303_5164_gb300.tenants import MIX_TYPES
+    rng = np.random.default_rng(seed)
+    types = rng.integers(0, len(MIX_TYPES), n)
+    grids = np.minimum(4096, np.floor(np.exp(rng.uniform(0.0, np.log(4097.0), n)))).astype(int)
+    return [(MIX_TYPES[t], seed, i, batch_sizes(MIX_TYPES[t], int(g))) for i, (t, g) in enumerate(zip(types, grids))]
 
 
 def generate(jobs, workers: int):
@@ -286,7 +320,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    jobs = mix_jobs()
+    jobs = mix_jobs() if args.workload == "mix" else batch_jobs()
     t_gen = time.time()
     inputs = generate(jobs, max(1, min(len(jobs), (os.cpu_count() or 2) // max(1, world))))
     t_gen = time.time() - t_gen
@@ -309,7 +343,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     cfg = K.config_default()
     cfg.device = local
-    cfg.max_tenants = 1024
+    cfg.max_tenants = 4096
     rt = K.Runtime(cfg, stream=stream.cuda_stream)
     hbm_gbs, peak_src = _measured_peaks()
     mp_ = rt.model_params()
@@ -455,7 +489,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "kernels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_co, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "kernels_per_step": n, "l2": "inputs larger than L2 (about "
+            "config": {"workload": WORKLOAD if args.workload == "mix" else BATCH_WORKLOAD, "kernels_per_step": n, "l2": "inputs larger than L2 (about "
                        f"{bytes_mix / 1e9:.1f} GB touched per step)", "slots_per_sm": rt.run_stats().slots_per_sm,
                        "multistream_streams": args.nstreams, "profiles": prof_src,
                        "parallelism": f"replicas x{world}"},
@@ -493,6 +527,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profiles", default="measured", choices=["measured", "none"])
+    ap.add_argument("--workload", default="mix", choices=["mix", "batch"],
+                    help="mix: 64 kernels of the eight types; batch: 512 tenants, log-uniform grids")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
