@@ -88,6 +88,39 @@ def batch_jobs(seed: int = 3, n: int = 512):
     return [(MIX_TYPES[t], seed, i, batch_sizes(MIX_TYPES[t], int(g))) for i, (t, g) in enumerate(zip(types, grids))]
 
 
+SERVE_WORKLOAD = ("serving: open-loop Poisson arrivals of the eight mix kernel types (equal mix), sizes of the "
+                  "64-kernel mix scaled 0.25x-4x log-uniform (five power-of-two buckets), admission by "
+                  "declared device-memory footprint (cap 150 GB) and in-flight slots (608 = SMs x 4)")
+SERVE_SCALES = (0.25, 0.5, 1.0, 2.0, 4.0)
+# log-uniform scale on [1/4, 4] rounded to the nearest power of two in log2
+SERVE_P = (0.125, 0.25, 0.25, 0.25, 0.125)
+
+
+def serve_size(name: str, s: float) -> dict:
+    """Size of a mix kernel scaled by s (work and bytes proportional to s)."""
+    from paper_1303_5164_gb300.tenants import SIZES_MIX
+    z = dict(SIZES_MIX[name])
+    if name == "gemm_f32":
+        z["M"] = int(z["M"] * s)
+    elif name == "spmv_csr":
+        z["nrows"] = int(z["nrows"] * s)
+    elif name in ("blackscholes", "triad", "hist256"):
+        z["n"] = int(z["n"] * s)
+    elif name == "pchase":
+        z["nchasers"] = int(z["nchasers"] * s)
+    elif name == "escape":
+        z["height"] = int(z["height"] * s)
+    elif name == "bitonic":
+        z["log2n"] = z["log2n"] + int(round(__import__("math").log2(s)))
+    return z
+
+
+def serve_jobs(seed: int = 4):
+    from paper_1303_5164_gb300.tenants import MIX_TYPES
+    return [(nm, seed, 8 * b + i, serve_size(nm, sc)) for b, sc in enumerate(SERVE_SCALES)
+            for i, nm in enumerate(MIX_TYPES)]
+
+
 def generate(jobs, workers: int):
     # spawn: the pool starts before any CUDA call and shares nothing with it
     if workers <= 1:
@@ -517,6 +550,156 @@ def run_ours(args):
     return 0
 
 
+def run_serve(args):
+    """Open-loop serving sweep: for each offered rate, Poisson arrivals for
+    --serve-seconds; an arrival waits in the client's FIFO until the runtime
+    admits it (kl_submit returns KL_EAGAIN while the in-flight slots or the
+    footprint cap are full) and a free output replica of its (type, size)
+    exists. Latency = arrival to the host seeing the completion. The same
+    arrival sequence drives the co-scheduled server and the plain multi-stream
+    FIFO server."""
+    import numpy as np
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    jobs = serve_jobs()
+    t_gen = time.time()
+    inputs = generate(jobs, max(1, min(len(jobs), (os.cpu_count() or 2) // max(1, world))))
+    t_gen = time.time() - t_gen
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1303_5164_gb300 import build as kb
+    from paper_1303_5164_gb300 import kernelet as K
+    from paper_1303_5164_gb300 import tenants as T
+    kb.build()
+    from paper_1303_5164_gb300.tenants import MIX_TYPES
+    base = [T.make(j[0], x) for j, x in zip(jobs, inputs)]
+    del inputs
+    reps = [[t] + [t.replica() for _ in range(args.serve_replicas - 1)] for t in base]
+    descs = [[K.make_desc(t.type, t.args, 0, t.footprint) for t in r] for r in reps]
+    torch.cuda.synchronize()
+    dev_gb = torch.cuda.memory_allocated() / 1e9
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    cfg = K.config_default()
+    cfg.device = local
+    cfg.max_tenants = 4 * n_sm
+    cfg.mem_cap_bytes = 150 * 10**9
+    stream = torch.cuda.Stream()  # the serving kernel holds its stream for the whole run
+    rt = K.Runtime(cfg, stream=stream.cuda_stream)
+    hbm_gbs, _ = _measured_peaks()
+    mp_ = rt.model_params()
+    mp_.dram_bytes_per_s = hbm_gbs * 1e9
+    rt.set_model_params(mp_)
+    profs, prof_doc = _load_profiles(K, None if args.profiles == "none" else PROFILES)
+    if profs:
+        rt.set_profiles(profs)
+        mp_.a0, mp_.b0 = prof_doc.get("a0", 1.0), prof_doc.get("b0", 0.0)
+        rt.set_model_params(mp_)
+    lib = K.lib()
+    import ctypes as C
+    hbuf = (K.U64 * 8192)()
+    nbuf = K.U32()
+
+    def one_rate(rate, mode, seed):
+        rng = np.random.default_rng(seed)
+        n_arr = max(1, int(rng.poisson(rate * args.serve_seconds)))
+        t_arr = np.sort(rng.uniform(0.0, args.serve_seconds, n_arr))
+        kinds = rng.integers(0, len(MIX_TYPES), n_arr)
+        buckets = rng.choice(len(SERVE_SCALES), n_arr, p=SERVE_P)
+        combo = buckets * len(MIX_TYPES) + kinds
+        free = [list(range(args.serve_replicas)) for _ in base]
+        owner = {}
+        lat, done_t = [], []
+        if mode == "cosched":
+            rt.serve_start(K.KL_SERVE_COSCHED, 0, 0)
+        else:
+            rt.serve_start(K.KL_BASE_MULTISTREAM, args.nstreams, 0)
+        h = C.c_uint64()
+        nxt = 0
+        t0 = time.perf_counter()
+        t_end = t0 + args.serve_seconds
+        while True:
+            now = time.perf_counter()
+            rc = lib.kl_reap(rt._h, hbuf, 8192, C.byref(nbuf))
+            if rc:
+                raise RuntimeError(f"kl_reap: {rc}")
+            for i in range(nbuf.value):
+                k, c, r = owner.pop(hbuf[i])
+                free[c].append(r)
+                lat.append(now - t0 - t_arr[k])
+                done_t.append(now - t0)
+            if now >= t_end:
+                break
+            while nxt < n_arr and t_arr[nxt] <= now - t0:
+                c = int(combo[nxt])
+                if not free[c]:
+                    break          # FIFO: the head waits for an output replica
+                r = free[c][-1]
+                rc = lib.kl_submit(rt._h, C.byref(descs[c][r]), C.byref(h))
+                if rc == K.KL_EAGAIN:
+                    break          # FIFO: the head waits for admission
+                if rc:
+                    raise RuntimeError(f"kl_submit: {lib.kl_strerror(rc).decode()}")
+                free[c].pop()
+                owner[h.value] = (nxt, c, r)
+                nxt += 1
+        admitted, in_flight = nxt, len(owner)
+        # arrivals are over: finish what was admitted (not counted as in-window throughput)
+        rc = rt.serve_stop(60_000_000_000)
+        if rc:
+            raise RuntimeError(f"serve run failed: {lib.kl_strerror(rc).decode()}")
+        done_in = len(done_t)
+        return {"offered_per_s": rate, "arrivals": n_arr, "admitted": admitted, "completed_in_window": done_in,
+                "throughput_per_s": done_in / args.serve_seconds,
+                "p50_ms": 1e3 * _pct(lat, 50) if lat else None, "p99_ms": 1e3 * _pct(lat, 99) if lat else None,
+                "not_admitted": n_arr - admitted, "in_flight_at_end": in_flight}
+
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    # warm-up: a short run of each server
+    keep = args.serve_seconds
+    args.serve_seconds = 0.3
+    for _ in range(max(1, args.warmup // 3)):
+        one_rate(1000.0, "cosched", 1)
+        one_rate(1000.0, "multistream", 1)
+    args.serve_seconds = keep
+    res = {"cosched": [], "multistream": []}
+    with ClockSampler(local) as clk, NvmlSampler(local) as nv:
+        for i, rate in enumerate(rates):
+            for mode in ("cosched", "multistream"):
+                res[mode].append(one_rate(rate, mode, 100 + i))
+                if rank == 0:
+                    print(mode, json.dumps(res[mode][-1]), file=sys.stderr, flush=True)
+    clocks = clk.summary()
+    nvs = nv.summary()
+    if nvs:
+        clocks = dict(nvs, nvidia_smi=clocks)
+    best = max(res["cosched"], key=lambda r: r["throughput_per_s"])
+    best_ms = max(res["multistream"], key=lambda r: r["throughput_per_s"])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * best["throughput_per_s"], "unit": "kernels/s",
+            "n_gpus": world, "steps": len(rates), "warmup": args.warmup,
+            "ms_per_step": 1e3 * args.serve_seconds, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "seconds_per_rate": args.serve_seconds,
+                       "rates_per_s": rates, "output_replicas": args.serve_replicas,
+                       "in_flight_slots": cfg.max_tenants, "mem_cap_bytes": cfg.mem_cap_bytes,
+                       "device_gb_allocated": round(dev_gb, 1), "multistream_streams": args.nstreams,
+                       "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+            "speedup_vs_multistream": best["throughput_per_s"] / best_ms["throughput_per_s"],
+            "serve": res, "clocks": clocks, "gpu_launches": 2 * len(rates),
+            "input_gen_s": round(t_gen, 1),
+        }
+        print(json.dumps(line))
+    rt.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -527,13 +710,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profiles", default="measured", choices=["measured", "none"])
-    ap.add_argument("--workload", default="mix", choices=["mix", "batch"],
-                    help="mix: 64 kernels of the eight types; batch: 512 tenants, log-uniform grids")
+    ap.add_argument("--workload", default="mix", choices=["mix", "batch", "serve"],
+                    help="mix: 64 kernels of the eight types; batch: 512 tenants, log-uniform grids; "
+                         "serve: open-loop arrival-rate sweep")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-rates", default="100,300,1000,3000,10000,20000")
+    ap.add_argument("--serve-replicas", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

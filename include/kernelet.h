@@ -267,6 +267,8 @@ typedef struct {
     uint64_t t_launch_ns;       /* device: run start (first CTA)                  */
     uint32_t slices;            /* slices pulled                                  */
     uint32_t blocks;            /* blocks executed                                */
+    uint64_t t_done_host_ns;    /* host steady clock when the runtime saw the
+                                   completion (serving: when it was reaped)       */
 } kl_tenant_stats;
 
 typedef struct {
@@ -284,7 +286,11 @@ typedef struct {
                                    its last (descriptors in, results out)        */
 } kl_run_stats;
 
-typedef enum { KL_BASE_SERIAL = 0, KL_BASE_MULTISTREAM = 1 } kl_baseline_mode;
+typedef enum {
+    KL_BASE_SERIAL = 0,       /* plain launches, one stream                      */
+    KL_BASE_MULTISTREAM = 1,  /* plain launches, round-robin over n streams      */
+    KL_SERVE_COSCHED = 2      /* kl_serve_start only: the persistent co-scheduler */
+} kl_baseline_mode;
 
 /* ------------------------------------------------------------------ runtime */
 
@@ -312,6 +318,44 @@ int kl_submit(kl_runtime* rt, const kl_kernel_desc* desc, kl_handle* out);
 /* Plan and start the pending set as one persistent co-scheduled launch on the
  * runtime's stream; returns without waiting. KL_EAGAIN if a run is in flight. */
 int kl_launch(kl_runtime* rt);
+
+/* Serving mode: continuous batching. Algorithm 1 lets kernels join the
+ * pending set R at any time; an arrival makes the scheduler choose the next
+ * co-schedule again over what is left of the running kernels plus the new
+ * ones (Section 2.2, Section 4.2). kl_serve_start(KL_SERVE_COSCHED) launches
+ * the persistent kernel and leaves it running; from then on each kl_submit is
+ * admitted straight to the running kernel: the descriptor is written into a
+ * ring in mapped host memory and the tail published with a release store; a
+ * dispatcher CTA on the device copies it in and re-plans. Completions come
+ * back through a completion queue in mapped memory while the kernel runs.
+ * mode KL_BASE_MULTISTREAM (nstreams streams) / KL_BASE_SERIAL is the plain
+ * comparator: each admitted kernel is launched at once on stream
+ * seq % nstreams.
+ * Admission, in every mode: at most cfg.max_tenants kernels in flight and
+ * their summed footprint_bytes within cfg.mem_cap_bytes (0 = no cap); beyond
+ * that kl_submit returns KL_EAGAIN and the caller retries later. Kernels still
+ * pending from kl_submit before the start are admitted first, in order, and
+ * keep their handles.
+ * idle_limit_ns (co-scheduled): the device ends the run after that long with
+ * no kernel in flight and no arrival (0 = 60 s); kl_submit then returns
+ * KL_ESTATE until kl_serve_stop and a new kl_serve_start. While serving,
+ * kl_launch, kl_launch_baseline and kl_drain return KL_ESTATE, and kl_poll /
+ * kl_wait / kl_get_stats / kl_reap see completions as they happen.
+ * The serving kernel occupies the runtime's stream until the run ends: work
+ * queued on that stream meanwhile (and a synchronize of it) waits for the end,
+ * so a kernel's inputs must be complete before its kl_submit (the device may
+ * start it at once) and other work goes on other streams.
+ * kl_serve_stop: no new admissions; every admitted kernel finishes, the run
+ * ends and is retired (KL_ETIMEDOUT after timeout_ns; call again). Returns the
+ * run's status. Errors: KL_ESTATE (not serving / already serving), KL_EAGAIN
+ * (a batch run is still in flight), KL_ENOMEM / KL_ECUDA. */
+int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint64_t idle_limit_ns);
+int kl_serve_stop(kl_runtime* rt, uint64_t timeout_ns);
+
+/* Serving: up to `cap` handles of kernels that completed since the last call,
+ * in completion order, into out[0..*n). The runtime keeps at most 2^20 such
+ * handles; older ones are dropped (their stats stay available). */
+int kl_reap(kl_runtime* rt, kl_handle* out, uint32_t cap, uint32_t* n);
 
 /* Execute the pending set with plain kernel launches instead of the
  * co-scheduler: KL_BASE_SERIAL = one stream in submit order; KL_BASE_MULTISTREAM

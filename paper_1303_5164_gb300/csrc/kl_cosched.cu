@@ -14,8 +14,15 @@
 // Markov model (Section 4.4) filled in on the host. Multi-stage kernels are
 // chains of grids: blocks of stage s run only after stage s-1 completed.
 //
+// Serving mode keeps the kernel running while the host keeps submitting:
+// kernels are numbered by submission and live in a ring of tenant slots; CTA 0
+// is a dispatcher that copies newly published descriptors from mapped host
+// memory into the device ring and re-plans on every arrival (Algorithm 1: a
+// new kernel joins R and the co-schedule is recomputed on the residuals).
+//
 // No wait in this kernel is unbounded: every spin has a globaltimer deadline
-// after which the run records KL_EDEVICE_TIMEOUT and every CTA returns.
+// after which the run records KL_EDEVICE_TIMEOUT (or, when serving and idle,
+// ends the run) and every CTA returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,11 +54,28 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// host-mapped words (system scope)
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_sys64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Co-resident CTAs per SM: 4 x 256 threads at up to 64 registers each.
 constexpr int kCtasPerSm = 4;
 
-enum : uint32_t { kActRun = 0, kActWait = 1, kActExit = 2, kActReplan = 3 };
+enum : uint32_t { kActRun = 0, kActWait = 1, kActExit = 2, kActReplan = 3, kActIntake = 4 };
 enum : int { kPulled = 0, kBlocked = 1, kExhausted = 2 };
 
 struct CtaCtl {
@@ -61,19 +85,29 @@ struct CtaCtl {
   uint32_t seq;
   int32_t trigger;
   int32_t wait_failed;
+  uint32_t from, to;   // dispatcher: kernels to copy in
 };
 
 __device__ __forceinline__ void set_error(RunDev* R, int32_t code, uint32_t info) {
   if (atomicCAS(reinterpret_cast<int*>(&R->error), 0, code) == 0) R->error_info = info;
 }
 
+__device__ __forceinline__ TenantDev& tenant(TenantDev* T, const RunDev* R, uint32_t seq) {
+  return T[seq & R->ring_mask];
+}
+__device__ __forceinline__ PhaseDev* phase(PhaseDev* P, const RunDev* R, uint32_t seq) {
+  return &P[seq & R->phase_mask];
+}
+
 // Thread 0 only: try to take the next slice of tenant t. `rank` is this CTA's
 // position among the slots of its SM that serve t: while the stage has fewer
 // blocks left than rank * numSM, the slot leaves them to lower ranks, so a
 // kernel with few blocks spreads one per SM instead of stacking on some SMs.
-__device__ __forceinline__ int try_pull(TenantDev* T, int32_t t, uint32_t rank, uint32_t n_sm, uint32_t& g0,
-                                        uint32_t& g1) {
-  TenantDev& d = T[t];
+__device__ __forceinline__ int try_pull(TenantDev* T, const RunDev* R, int32_t t, uint32_t rank, uint32_t n_sm,
+                                        uint32_t& g0, uint32_t& g1) {
+  TenantDev& d = tenant(T, R, (uint32_t)t);
+  // serving: a phase read just before the slot was refilled names an older kernel
+  if (d.index != (uint32_t)t) return kExhausted;
   const uint32_t total = d.total;
   uint32_t n = ld_relaxed(&d.next);
   if (n >= total) return kExhausted;
@@ -94,11 +128,13 @@ __device__ __forceinline__ int try_pull(TenantDev* T, int32_t t, uint32_t rank, 
 }
 
 // FindCoSchedule on the device (Algorithm 1, procedure), warp 0 of one CTA.
-// Pending = kernels with blocks not yet handed out. For every pair of pending
-// kernels CP depends only on their types, so the best pair of a type pair is
-// its two lowest submit indices; the winner is the largest CP among unpruned
-// type pairs (all pairs when every one is pruned), ties to the smallest
-// (i, j). One pending kernel runs alone on every slot; none ends the run.
+// Pending = kernels with blocks not yet handed out, among sequence numbers
+// [scan_lo, end) (end = kernels submitted; in serving mode, copied in). For
+// every pair of pending kernels CP depends only on their types, so the best
+// pair of a type pair is its two lowest sequence numbers; the winner is the
+// largest CP among unpruned type pairs (all pairs when every one is pruned),
+// ties to the smallest (i, j). One pending kernel runs alone on every slot;
+// none ends a batch run, or idles a serving run until the next arrival.
 __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, int32_t trigger) {
   const int lane = threadIdx.x & 31;
   int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
@@ -109,20 +145,25 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
   int32_t lowp[6];
   uint32_t nlow = 0;
   int32_t lowms = -1;  // lowest pending kernel with more than one stage
-  const uint32_t n = R->n_tenants;
-  for (uint32_t base = 0; base < n; base += 32) {
+  const uint32_t lo = ld_relaxed(&R->scan_lo);
+  const uint32_t hi = R->serve ? ld_acquire(&R->intake) : R->n_tenants;
+  int32_t first_pending = -1;
+  for (uint32_t base = lo; base < hi; base += 32) {
     const uint32_t i = base + lane;
-    bool pend = false;
+    bool pend = false, multi = false;
     uint32_t ty = 0;
-    if (i < n) {
-      ty = T[i].type;
-      pend = ld_relaxed(&T[i].next) < T[i].total;
+    if (i < hi) {
+      const TenantDev& d = tenant(T, R, i);
+      ty = d.type;
+      pend = ld_relaxed(&d.next) < d.total;
+      multi = d.nstages > 1;
     }
     const uint32_t pb = __ballot_sync(0xffffffffu, pend);
     npend += __popc(pb);
+    if (pb && first_pending < 0) first_pending = (int32_t)(base + __ffs(pb) - 1);
     if (base < 64) pmask |= (unsigned long long)pb << base;
     for (uint32_t m = pb; m && nlow < 6; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
-    const uint32_t msb = __ballot_sync(0xffffffffu, pend && T[min(i, n - 1)].nstages > 1);
+    const uint32_t msb = __ballot_sync(0xffffffffu, pend && multi);
     if (msb && lowms < 0) lowms = (int32_t)(base + __ffs(msb) - 1);
 #pragma unroll
     for (int t = 0; t < KL_T_COUNT; ++t) {
@@ -135,8 +176,10 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
     }
   }
   if (lane != 0) return;
+  // kernels below the first pending one are all handed out: skip them next time
+  st_release(&R->scan_lo, first_pending >= 0 ? (uint32_t)first_pending : hi);
   PhaseDev ph;
-  ph.A = -1;
+  ph.A = R->serve ? kPhaseIdle : kPhaseEnd;
   ph.B = -1;
   ph.slots_a = R->slots;
   ph.slots_b = 0;
@@ -144,11 +187,13 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
   ph.trigger = trigger;
   ph.n_pending = npend;
   ph.pending = pmask;
+  ph.intake_seen = hi;
+  ph.pad2 = 0;
   if (npend == 1) {
     for (int t = 0; t < KL_T_COUNT; ++t)
       if (low1[t] >= 0) ph.A = low1[t];
   } else if (npend >= 2) {
-    for (int pass = 0; pass < 2 && ph.A < 0; ++pass) {
+    for (int pass = 0; pass < 2; ++pass) {
       double best = 0.0;
       int32_t bi = -1, bj = -1;
       for (int ta = 0; ta < KL_T_COUNT; ++ta) {
@@ -164,7 +209,7 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
             i = min(low1[ta], low1[tb]);
             j = max(low1[ta], low1[tb]);
           }
-          const uint32_t tyi = T[i].type, tyj = T[j].type;
+          const uint32_t tyi = tenant(T, R, i).type, tyj = tenant(T, R, j).type;
           if (pass == 0 && !R->allowed[tyi][tyj]) continue;
           const double c = R->cp[tyi][tyj];
           // CP equal within 1e-12 is a tie, resolved to the smaller (i, j)
@@ -180,28 +225,29 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
         ph.A = bi;
         ph.B = bj;
         ph.cp = best;
-        ph.slots_a = R->slots_a[T[bi].type][T[bj].type];
+        ph.slots_a = R->slots_a[tenant(T, R, bi).type][tenant(T, R, bj).type];
         ph.slots_b = R->slots - ph.slots_a;
+        break;
       }
     }
   }
   // backfill candidates: the next pending kernel of A's type and of B's type
-  // (more of the work the pair is doing), then the lowest pending indices
+  // (more of the work the pair is doing), then the lowest pending multi-stage
+  // kernel (a long chain of dependent grids: started early, its stage
+  // barriers overlap other work instead of forming the tail of the run), then
+  // the lowest pending sequence numbers
   for (int f = 0; f < 4; ++f) ph.fill[f] = -1;
   uint32_t c = 0;
   if (ph.A >= 0 && (R->flags & KL_CFG_FILL_TYPES)) {
-    const uint32_t ta = T[ph.A].type;
+    const uint32_t ta = tenant(T, R, ph.A).type;
     const int32_t sa = low1[ta] != ph.A ? low1[ta] : low2[ta];
     if (sa >= 0 && sa != ph.B) ph.fill[c++] = sa;
     if (ph.B >= 0) {
-      const uint32_t tb = T[ph.B].type;
+      const uint32_t tb = tenant(T, R, ph.B).type;
       const int32_t sb = low1[tb] != ph.B ? low1[tb] : low2[tb];
       if (sb >= 0 && sb != ph.A && (c == 0 || sb != ph.fill[0])) ph.fill[c++] = sb;
     }
   }
-  // then the lowest pending multi-stage kernel (a long chain of dependent
-  // grids: started early, its stage barriers overlap other work instead of
-  // forming the tail of the run), then the lowest pending indices
   if (lowms >= 0 && c < 4 && lowms != ph.A && lowms != ph.B && (c == 0 || lowms != ph.fill[0]) &&
       (c < 2 || lowms != ph.fill[1]))
     ph.fill[c++] = lowms;
@@ -211,23 +257,24 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
     if (!dup) ph.fill[c++] = lowp[f];
   }
   const uint32_t seq = seq_old + 1;
-  if (seq >= R->max_phases) {
+  if (!R->serve && seq >= R->max_phases) {
     set_error(R, KL_EOVERFLOW, seq);
-    ph.A = -1;
+    ph.A = kPhaseEnd;
     ph.B = -1;
   }
   // block counts at this instant: per-phase measured progress of each kernel
-  ph.done_a = ph.A >= 0 ? ld_relaxed(&T[ph.A].done) : 0u;
-  ph.done_b = ph.B >= 0 ? ld_relaxed(&T[ph.B].done) : 0u;
+  ph.done_a = ph.A >= 0 ? ld_relaxed(&tenant(T, R, ph.A).done) : 0u;
+  ph.done_b = ph.B >= 0 ? ld_relaxed(&tenant(T, R, ph.B).done) : 0u;
   {
-    const int32_t pa = __ldcg(&P[seq_old].A), pb = __ldcg(&P[seq_old].B);
-    ph.prev_done_a = pa >= 0 ? ld_relaxed(&T[pa].done) : 0u;
-    ph.prev_done_b = pb >= 0 ? ld_relaxed(&T[pb].done) : 0u;
+    const int32_t pa = __ldcg(&phase(P, R, seq_old)->A), pb = __ldcg(&phase(P, R, seq_old)->B);
+    ph.prev_done_a = pa >= 0 ? ld_relaxed(&tenant(T, R, pa).done) : 0u;
+    ph.prev_done_b = pb >= 0 ? ld_relaxed(&tenant(T, R, pb).done) : 0u;
   }
   ph.t = gtimer();
-  P[min(seq, R->max_phases - 1)] = ph;
+  const uint32_t slot = R->serve ? seq : min(seq, R->max_phases - 1);
+  *phase(P, R, slot) = ph;
   __threadfence();
-  st_release(&R->phase_seq, min(seq, R->max_phases - 1));
+  st_release(&R->phase_seq, slot);
 }
 
 __device__ __forceinline__ void complete_tenant(TenantDev& d, RunDev* R) {
@@ -235,12 +282,99 @@ __device__ __forceinline__ void complete_tenant(TenantDev& d, RunDev* R) {
   d.t_end = now;
   __threadfence();
   st_release(&d.status, KL_DONE);
+  if (R->serve) {
+    // the host reaps completions from the queue while the run goes on: the
+    // record first, then the queue entry that publishes it
+    ServeDone& r = R->host_done[d.index & R->ring_mask];
+    r.slices = d.slices;
+    r.blocks = d.total;
+    r.t_start = d.t_start;
+    r.t_end = now;
+    r.seq1 = d.index + 1u;
+    __threadfence_system();
+    const uint32_t pos = atomicAdd(&R->cq_pos, 1u);
+    st_release_sys64(R->host_cq + (pos & R->ring_mask), ((unsigned long long)(pos + 1u) << 32) | d.index);
+  }
   atomicAdd(&R->n_complete, 1u);
   atomicMax(&R->t_end, now);
 }
 
+// Serving mode, CTA 0: copy arrivals in, re-plan, end the run on request.
+__device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl) {
+  const int tid = threadIdx.x;
+  unsigned long long last_arrival = gtimer();
+  unsigned long long stop_since = 0;
+  for (;;) {
+    if (tid == 0) {
+      ctl.action = kActWait;
+      const unsigned long long now = gtimer();
+      const uint32_t intake = ld_relaxed(&R->intake);
+      const uint32_t tail = ld_acquire_sys(R->host_ctl);
+      const uint32_t room = ld_relaxed(&R->scan_lo) + R->ring_mask + 1u;  // slots the device may fill
+      if (ld_relaxed(reinterpret_cast<uint32_t*>(&R->error)) != 0) {
+        ctl.action = kActExit;
+      } else if (tail > intake && room > intake) {
+        ctl.action = kActIntake;
+        ctl.from = intake;
+        ctl.to = min(tail, room);
+        last_arrival = now;
+      } else {
+        const bool quiet = ld_relaxed(&R->n_complete) == intake && tail == intake;
+        const bool stop = ld_acquire_sys(R->host_ctl + 32) != 0;
+        if (quiet && (stop || now - last_arrival > R->idle_limit_ns)) {
+          // end of the run: publish the final phase (claimed like a re-plan)
+          if (stop_since == 0) stop_since = now;
+          const uint32_t seq = ld_acquire(&R->phase_seq);
+          if (ld_relaxed(&R->phase_claim) == seq && atomicCAS(&R->phase_claim, seq, seq + 1) == seq) {
+            PhaseDev* e = phase(P, R, seq + 1);
+            e->A = kPhaseEnd;
+            e->B = -1;
+            e->intake_seen = intake;
+            e->t = now;
+            __threadfence();
+            st_release(&R->phase_seq, seq + 1);
+            ctl.action = kActExit;
+          } else if (now - stop_since > R->wait_limit_ns) {
+            set_error(R, KL_EDEVICE_TIMEOUT, 4u);
+            ctl.action = kActExit;
+          }
+        }
+      }
+      if (ctl.action == kActWait) __nanosleep(256);
+    }
+    __syncthreads();
+    const uint32_t action = ctl.action;
+    if (action == kActExit) return;
+    if (action == kActIntake) {
+      if (tid < 32) {
+        // 256-byte descriptors, 8 bytes per lane; the host zeroed the dynamic part
+        for (uint32_t s = ctl.from; s < ctl.to; ++s) {
+          const unsigned long long* src =
+              reinterpret_cast<const unsigned long long*>(&R->host_ring[s & R->ring_mask]);
+          unsigned long long* dst = reinterpret_cast<unsigned long long*>(&T[s & R->ring_mask]);
+          dst[tid] = ld_volatile64(src + tid);
+        }
+        __threadfence();
+        __syncwarp();
+        // re-plan on arrival (Algorithm 1); if a re-plan is already running,
+        // the workers see intake > intake_seen and ask for another
+        uint32_t seq = 0, mine = 0;
+        if (tid == 0) {
+          st_release(&R->intake, ctl.to);
+          seq = ld_acquire(&R->phase_seq);
+          mine = ld_relaxed(&R->phase_claim) == seq && atomicCAS(&R->phase_claim, seq, seq + 1) == seq;
+        }
+        mine = __shfl_sync(0xffffffffu, mine, 0);
+        seq = __shfl_sync(0xffffffffu, seq, 0);
+        if (mine) replan(T, R, P, seq, -1);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev* __restrict__ T, RunDev* __restrict__ R,
-                                                             PhaseDev* __restrict__ P) {
+                                                                      PhaseDev* __restrict__ P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaCtl ctl;
   __shared__ uint32_t s_slot;
@@ -252,6 +386,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     atomicCAS(&R->t_launch, 0ull, gtimer());
   }
   __syncthreads();
+  if (R->serve && blockIdx.x == 0) {
+    dispatcher(T, R, P, ctl);
+    if (tid == 0) atomicAdd(&R->ctas_done, 1u);
+    return;
+  }
   const uint32_t slot = s_slot;
   const uint32_t S = R->slots;
   const uint32_t n_sm = gridDim.x / S;
@@ -263,27 +402,37 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     if (tid == 0) {
       ctl.action = kActWait;
       ctl.tenant = -1;
+      bool idle = false;
       if (ld_relaxed(reinterpret_cast<uint32_t*>(&R->error)) != 0) {
         ctl.action = kActExit;
       } else {
         const uint32_t seq = ld_acquire(&R->phase_seq);
-        PhaseDev ph;  // published by another CTA: read through L2
-        ph.A = __ldcg(&P[seq].A);
-        ph.B = __ldcg(&P[seq].B);
-        ph.slots_a = __ldcg(&P[seq].slots_a);
-        if (ph.A == -1) {
+        PhaseDev* pp = phase(P, R, seq);  // published by another CTA: read through L2
+        PhaseDev ph;
+        ph.A = __ldcg(&pp->A);
+        ph.B = __ldcg(&pp->B);
+        ph.slots_a = __ldcg(&pp->slots_a);
+        if (ph.A == kPhaseEnd) {
           ctl.action = kActExit;
         } else {
-          bool need_replan = (ph.A == -2);
+          bool need_replan = ph.A == kPhasePlan;
           int32_t trig = -1;
-          if (!need_replan) {
+          // serving: kernels arrived after this plan was made; re-plan now
+          if (R->serve && ld_relaxed(&R->intake) > __ldcg(&pp->intake_seen) &&
+              ld_relaxed(&R->phase_claim) == seq && atomicCAS(&R->phase_claim, seq, seq + 1) == seq) {
+            ctl.action = kActReplan;
+            ctl.seq = seq;
+            ctl.trigger = -1;
+          }
+          idle = ph.A == kPhaseIdle;
+          if (ph.A >= 0 && ctl.action == kActWait) {
             const bool mine_is_b = ph.B >= 0 && slot >= ph.slots_a;
             const int32_t t1 = mine_is_b ? ph.B : ph.A;
             const int32_t t2 = mine_is_b ? ph.A : ph.B;
             const uint32_t rank1 = mine_is_b ? slot - ph.slots_a : slot;
             const uint32_t rank2 = mine_is_b ? slot : slot + (S - ph.slots_a);
             uint32_t g0 = 0, g1 = 0;
-            int r = try_pull(T, t1, rank1, n_sm, g0, g1);
+            int r = try_pull(T, R, t1, rank1, n_sm, g0, g1);
             if (r == kPulled) {
               ctl.action = kActRun;
               ctl.tenant = t1;
@@ -301,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
                 ctl.seq = seq;
                 ctl.trigger = trig;
               } else if (t2 >= 0) {
-                int r2 = try_pull(T, t2, rank2, n_sm, g0, g1);
+                int r2 = try_pull(T, R, t2, rank2, n_sm, g0, g1);
                 if (r2 == kPulled) {
                   ctl.action = kActRun;
                   ctl.tenant = t2;
@@ -325,10 +474,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
           // pending kernel instead of idling
           if (ctl.action == kActWait && (R->flags & KL_CFG_BACKFILL) && ph.A >= 0) {
             for (int f = 0; f < 4; ++f) {
-              const int32_t c = __ldcg(&P[seq].fill[f]);
+              const int32_t c = __ldcg(&pp->fill[f]);
               if (c < 0) break;
               uint32_t g0 = 0, g1 = 0;
-              if (try_pull(T, c, 0u, n_sm, g0, g1) == kPulled) {
+              if (try_pull(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
                 ctl.action = kActRun;
                 ctl.tenant = c;
                 ctl.g0 = g0;
@@ -342,7 +491,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
       if (ctl.action == kActWait) {
         const unsigned long long now = gtimer();
         if (wait_since == 0) wait_since = now;
-        if (now - wait_since > limit) {
+        // an idle serving run waits for arrivals; its dispatcher ends the run
+        const unsigned long long lim = (R->serve && idle) ? R->idle_limit_ns + limit : limit;
+        if (now - wait_since > lim) {
           set_error(R, KL_EDEVICE_TIMEOUT, 1u);
           ctl.action = kActExit;
         } else {
@@ -360,8 +511,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     if (action == kActReplan) {
       if (tid < 32) replan(T, R, P, ctl.seq, ctl.trigger);
     } else if (action == kActRun) {
-      const int32_t t = ctl.tenant;
-      TenantDev& d = T[t];
+      TenantDev& d = tenant(T, R, (uint32_t)ctl.tenant);
       const uint32_t type = d.type;
       uint32_t g = ctl.g0;
       const uint32_t g1 = ctl.g1;

@@ -46,8 +46,26 @@ struct PhaseDev {
   uint32_t done_a, done_b;     // blocks finished by this phase's A, B when it was published
   uint32_t prev_done_a;        // ... and by the previous phase's A, B at the same moment
   uint32_t prev_done_b;
+  uint32_t intake_seen;        // kernels known to the device when the phase was chosen
+  uint32_t pad2;
 };
-static_assert(sizeof(PhaseDev) == 80, "PhaseDev layout");
+static_assert(sizeof(PhaseDev) == 88, "PhaseDev layout");
+
+// Serving mode: per-kernel completion record in mapped host memory, written
+// by the device before the kernel's entry in the completion queue.
+struct ServeDone {
+  uint32_t seq1;                 // sequence number + 1
+  uint32_t slices;
+  uint32_t blocks;
+  uint32_t pad;
+  unsigned long long t_start;    // globaltimer
+  unsigned long long t_end;
+};
+static_assert(sizeof(ServeDone) == 32, "ServeDone layout");
+
+// Phase entries with A < 0: -1 ends the run, -2 asks for the first plan,
+// -3 means nothing is pending (serving mode waits for arrivals).
+constexpr int32_t kPhaseEnd = -1, kPhasePlan = -2, kPhaseIdle = -3;
 
 // Run-wide state of one co-scheduled launch.
 struct alignas(128) RunDev {
@@ -57,8 +75,15 @@ struct alignas(128) RunDev {
   uint32_t max_phases;
   uint32_t n_types;
   uint32_t flags;              // kl_config.flags
-  uint32_t pad0;
+  uint32_t serve;              // 1: serving mode (tenant ring, dispatcher CTA 0)
   unsigned long long wait_limit_ns;
+  uint32_t ring_mask;          // tenant slots - 1 (power of two); tenant seq -> slot
+  uint32_t phase_mask;         // phase slots - 1 (power of two)
+  unsigned long long idle_limit_ns;   // serving: exit after this long without arrivals
+  TenantDev* host_ring;        // serving: descriptors written by the host (mapped memory)
+  uint32_t* host_ctl;          // serving: [0] published tail, [32] stop request (mapped)
+  ServeDone* host_done;        // serving: per tenant slot, completion record (mapped)
+  unsigned long long* host_cq; // serving: completion queue, entry k = (k + 1) << 32 | seq (mapped)
   double cp[KL_T_COUNT][KL_T_COUNT];          // CP of (type row as K1, type col as K2)
   uint32_t slots_a[KL_T_COUNT][KL_T_COUNT];   // slots of the K1 (row) kernel
   uint32_t allowed[KL_T_COUNT][KL_T_COUNT];   // 1 = pair survives pruning
@@ -71,6 +96,9 @@ struct alignas(128) RunDev {
   uint32_t ctas_done;
   unsigned long long t_launch;       // globaltimer, first CTA
   unsigned long long t_end;          // globaltimer, last completion
+  uint32_t intake;                   // serving: kernels copied into the device ring
+  uint32_t scan_lo;                  // lowest sequence number that may still be pending
+  uint32_t cq_pos;                   // serving: completion queue entries written
   alignas(128) uint32_t sm_ticket[kMaxSM];
 };
 

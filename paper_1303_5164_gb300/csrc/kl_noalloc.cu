@@ -31,9 +31,12 @@ namespace {
 
 constexpr uint32_t kMaxT = KL_NOALLOC_MAX_TENANTS;
 constexpr uint32_t kMaxPhases = 4 * kMaxT + 16;
+constexpr uint32_t kPhaseSlots = 512;  // the device indexes phases modulo a power of two
+static_assert((kMaxT & (kMaxT - 1)) == 0, "tenant slots must be a power of two");
+static_assert(kPhaseSlots >= kMaxPhases, "phase slots");
 constexpr size_t kRunOff = sizeof(TenantDev) * kMaxT;
 constexpr size_t kPhaseOff = (kRunOff + sizeof(RunDev) + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kPhaseOff + sizeof(PhaseDev) * kMaxPhases;
+constexpr size_t kScratchBytes = kPhaseOff + sizeof(PhaseDev) * kPhaseSlots;
 constexpr int kMaxDevices = 64;
 
 // Device scratch of the allocation-free path (the only storage it uses).
@@ -114,6 +117,8 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
   R.max_phases = 4 * n + 16;
   R.n_types = KL_T_COUNT;
   R.flags = KL_CFG_BACKFILL;
+  R.ring_mask = kMaxT - 1;
+  R.phase_mask = kPhaseSlots - 1;
   R.wait_limit_ns = wait_limit_ns ? wait_limit_ns : 2000000000ull;
   for (uint32_t a = 0; a < KL_T_COUNT; ++a)
     for (uint32_t b = 0; b < KL_T_COUNT; ++b) {

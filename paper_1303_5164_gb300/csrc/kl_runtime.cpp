@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
@@ -178,7 +179,23 @@ struct Record {
   kl_handle handle = 0;
 };
 
-enum RunKind { kNone = 0, kCosched = 1, kBaseline = 2 };
+enum RunKind { kNone = 0, kCosched = 1, kBaseline = 2, kServe = 3, kServeBase = 4 };
+
+// One kernel of a serving run, by sequence number.
+struct ServeRec {
+  uint64_t t_submit;
+  uint64_t footprint;
+  uint64_t t_done_host;
+  uint32_t state;    // KL_RUNNING until reaped
+  uint32_t total;    // thread blocks
+  ServeDone done;    // device record (co-scheduled serving)
+};
+
+uint32_t pow2_at_least(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return (uint32_t)p;
+}
 
 }  // namespace
 
@@ -189,6 +206,7 @@ struct kl_runtime {
   cudaStream_t stream = nullptr;
   uint32_t n_sm = 0, slots = 0, occupancy = 0;
   uint32_t cap = 0, cap_phases = 0;
+  uint32_t ring_slots = 0, phase_slots = 0;  // powers of two >= cap, cap_phases
   TenantDev* d_tenants = nullptr;
   RunDev* d_run = nullptr;
   PhaseDev* d_phases = nullptr;
@@ -221,16 +239,39 @@ struct kl_runtime {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> side_join;
   cudaEvent_t ev_fork = nullptr;
+  // serving (kind kServe: persistent kernel fed through mapped memory;
+  // kServeBase: one plain launch per arrival on stream seq % s_nstreams)
+  bool serve_on = false;            // between kl_serve_start and kl_serve_stop
+  int serve_mode = 0;
+  uint32_t s_ring = 0, s_phase_slots = 0;
+  TenantDev* sd_ring = nullptr;     // device tenant ring
+  PhaseDev* sd_phases = nullptr;    // device phase ring
+  PhaseDev* sh_phases = nullptr;    // pinned copy of the phase ring after the run
+  TenantDev* sm_ring = nullptr;     // mapped: descriptors the host publishes
+  uint32_t* sm_ctl = nullptr;       // mapped: [0] tail, [32] stop request
+  ServeDone* sm_done = nullptr;     // mapped: completion records
+  unsigned long long* sm_cq = nullptr;  // mapped: completion queue
+  TenantDev* sdm_ring = nullptr;    // device addresses of the mapped buffers
+  uint32_t* sdm_ctl = nullptr;
+  ServeDone* sdm_done = nullptr;
+  unsigned long long* sdm_cq = nullptr;
+  uint32_t s_tail = 0, s_head = 0, s_inflight = 0, s_nstreams = 0;
+  uint64_t s_footprint = 0;
+  std::vector<ServeRec> s_recs;
+  std::vector<std::deque<std::pair<uint32_t, cudaEvent_t>>> s_stream_q;  // kServeBase
+  std::vector<cudaEvent_t> s_free_ev;
+  std::deque<kl_handle> completed;  // serving: handles completed, not yet returned by kl_reap
+  bool s_joined = false;            // kServeBase: side streams joined and ev_done recorded
 };
 
 namespace {
 
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? KL_OK : KL_ECUDA; }
 
-kl_handle make_handle(uint64_t run, uint32_t idx) { return (run << 24) | (uint64_t)(idx + 1); }
+kl_handle make_handle(uint64_t run, uint32_t idx) { return (run << 32) | (uint64_t)(idx + 1u); }
 void split_handle(kl_handle h, uint64_t* run, uint32_t* idx) {
-  *run = h >> 24;
-  *idx = (uint32_t)(h & 0xffffffu) - 1;
+  *run = h >> 32;
+  *idx = (uint32_t)(h & 0xffffffffu) - 1u;
 }
 
 // CP table for every pair of types in `mask` (Section 4.4 model + Section 4.3
@@ -275,10 +316,129 @@ void record_history(kl_runtime* rt, uint64_t id, std::vector<Record>&& recs) {
   while (rt->history.size() > 8) rt->history.erase(rt->history.begin());
 }
 
+// Serving: a kernel of the serving run has completed (lock held).
+void serve_finish(kl_runtime* rt, uint32_t seq, uint32_t state) {
+  ServeRec& r = rt->s_recs[seq];
+  r.state = state;
+  r.t_done_host = now_ns();
+  rt->s_inflight--;
+  rt->s_footprint -= r.footprint;
+  rt->completed.push_back(make_handle(rt->flight_id, seq));
+  while (rt->completed.size() > (1u << 20)) rt->completed.pop_front();
+}
+
+// Serving: collect the completions published since the last call (lock held).
+// Co-scheduled: completion queue entries in mapped memory, tagged with their
+// position so a stale entry is never mistaken for a new one. Plain launches:
+// per stream, the oldest outstanding event (kernels of a stream finish in order).
+int serve_reap(kl_runtime* rt) {
+  if (rt->kind == kServe) {
+    const uint32_t mask = rt->s_ring - 1u;
+    for (;;) {
+      const unsigned long long e = __atomic_load_n(&rt->sm_cq[rt->s_head & mask], __ATOMIC_ACQUIRE);
+      if ((uint32_t)(e >> 32) != rt->s_head + 1u) break;
+      const uint32_t seq = (uint32_t)e;
+      rt->s_head++;
+      if (seq >= rt->s_recs.size() || rt->s_recs[seq].state != KL_RUNNING) continue;
+      rt->s_recs[seq].done = rt->sm_done[seq & mask];
+      serve_finish(rt, seq, KL_DONE);
+    }
+  } else if (rt->kind == kServeBase) {
+    for (auto& q : rt->s_stream_q) {
+      while (!q.empty()) {
+        cudaError_t e = cudaEventQuery(q.front().second);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) return KL_ECUDA;
+        serve_finish(rt, q.front().first, KL_DONE);
+        rt->s_free_ev.push_back(q.front().second);
+        q.pop_front();
+      }
+    }
+  }
+  return KL_OK;
+}
+
+// Retire a serving run whose stream work has completed (lock held).
+int retire_serve(kl_runtime* rt) {
+  int run_err = KL_OK;
+  serve_reap(rt);
+  uint64_t t_launch = 0;
+  if (rt->kind == kServe) {
+    const RunDev& R = *rt->h_run;
+    run_err = R.error;
+    t_launch = R.t_launch;
+    const uint64_t np = (uint64_t)R.phase_seq + 1;
+    const uint64_t first = np > rt->s_phase_slots ? np - rt->s_phase_slots : 0;
+    rt->last_phases.clear();
+    for (uint64_t k = first; k < np; ++k) {
+      const PhaseDev& p = rt->sh_phases[k & (rt->s_phase_slots - 1)];
+      kl_phase q{};
+      q.A = p.A;
+      q.B = p.B;
+      q.slots_a = p.slots_a;
+      q.slots_b = p.slots_b;
+      q.cp = p.cp;
+      q.t_ns = p.t;
+      q.trigger = p.trigger;
+      q.n_pending = p.n_pending;
+      q.pending_mask = p.pending;
+      q.done_a = p.done_a;
+      q.done_b = p.done_b;
+      q.prev_done_a = p.prev_done_a;
+      q.prev_done_b = p.prev_done_b;
+      rt->last_phases.push_back(q);
+    }
+    rt->last = kl_run_stats{};
+    rt->last.n_phases = (uint32_t)std::min<uint64_t>(np, 0xffffffffu);
+    rt->last.t_launch_ns = R.t_launch;
+    rt->last.t_end_ns = R.t_end;
+  } else {
+    rt->last = kl_run_stats{};
+    rt->last_phases.clear();
+  }
+  const uint32_t n = (uint32_t)rt->s_recs.size();
+  std::vector<Record> recs(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    ServeRec& s = rt->s_recs[i];
+    Record& r = recs[i];
+    r.handle = make_handle(rt->flight_id, i);
+    r.st.t_submit_ns = s.t_submit;
+    r.st.t_done_host_ns = s.t_done_host;
+    r.st.t_launch_ns = t_launch;
+    if (s.state == KL_DONE) {
+      r.st.state = KL_DONE;
+      r.st.t_start_ns = s.done.t_start;
+      r.st.t_end_ns = s.done.t_end;
+      r.st.slices = s.done.slices;
+      r.st.blocks = s.done.blocks;
+      if (rt->kind == kServeBase) r.st.blocks = s.total;
+    } else {
+      // admitted but never completed: the run ended on an error (or before the
+      // device took the kernel in)
+      r.st.state = KL_ERROR;
+      r.st.error = run_err ? run_err : KL_ESTATE;
+    }
+  }
+  rt->last.n_tenants = n;
+  rt->last.error = run_err;
+  rt->last.slots_per_sm = rt->slots;
+  rt->last.grid_ctas = rt->slots * rt->n_sm;
+  float ms = 0.f;
+  rt->last.kernel_ns = cudaEventElapsedTime(&ms, rt->ev_k0, rt->ev_k1) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
+  rt->last.run_ns = cudaEventElapsedTime(&ms, rt->ev_start, rt->ev_done) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
+  record_history(rt, rt->flight_id, std::move(recs));
+  rt->s_recs.clear();
+  rt->s_recs.shrink_to_fit();
+  rt->in_flight = false;
+  rt->kind = kNone;
+  return run_err;
+}
+
 // Move a finished run into the history. Caller holds the lock and has seen
 // ev_done complete.
 int retire(kl_runtime* rt) {
   if (!rt->in_flight) return KL_OK;
+  if (rt->kind == kServe || rt->kind == kServeBase) return retire_serve(rt);
   const uint32_t n = (uint32_t)rt->flight.size();
   std::vector<Record> recs(n);
   int run_err = KL_OK;
@@ -366,6 +526,10 @@ int retire(kl_runtime* rt) {
 // Non-blocking check of the in-flight run.
 int progress(kl_runtime* rt) {
   if (!rt->in_flight) return KL_OK;
+  if (rt->kind == kServe || rt->kind == kServeBase) {
+    if (serve_reap(rt) != KL_OK) return KL_ECUDA;
+    if (rt->kind == kServeBase && !rt->s_joined) return KL_EAGAIN;
+  }
   cudaError_t e = cudaEventQuery(rt->ev_done);
   if (e == cudaErrorNotReady) return KL_EAGAIN;
   if (e != cudaSuccess) return KL_ECUDA;
@@ -383,6 +547,76 @@ int wait_flight(kl_runtime* rt, std::unique_lock<std::mutex>& lk, uint64_t timeo
     std::this_thread::sleep_for(std::chrono::microseconds(20));
     lk.lock();
   }
+}
+
+// Plain-launch server: join the side streams into the runtime stream and
+// record the run's end event (lock held).
+int serve_join(kl_runtime* rt) {
+  int rc = KL_OK;
+  for (uint32_t k = 0; k < rt->s_nstreams && !rc; ++k) {
+    rc = cuda_ok(cudaEventRecord(rt->side_join[k], rt->side[k]));
+    if (!rc) rc = cuda_ok(cudaStreamWaitEvent(rt->stream, rt->side_join[k], 0));
+  }
+  if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, rt->stream));
+  if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_done, rt->stream));
+  rt->s_joined = true;
+  return rc;
+}
+
+// A slice never exceeds the kernel, and the queue counter (which can overshoot
+// by one slice per CTA when a kernel runs out) stays below 2^32.
+uint32_t clamp_slice(const kl_runtime* rt, uint32_t slice, uint32_t total) {
+  const uint64_t ctas = (uint64_t)rt->n_sm * rt->slots;
+  uint64_t sl = std::min<uint64_t>(slice, total);
+  while (sl > 1 && (uint64_t)total + sl * (ctas + 1) >= (1ull << 32)) sl >>= 1;
+  return (uint32_t)std::max<uint64_t>(sl, 1);
+}
+
+// Serving: admit one kernel to the running server (lock held). Co-scheduled:
+// write the descriptor into the mapped ring, then publish the new tail with a
+// release store; the device's dispatcher copies it in and re-plans. Plain
+// launches: launch it now on stream seq % nstreams.
+int serve_publish(kl_runtime* rt, TenantDev td, uint64_t footprint, kl_handle* out) {
+  int p = progress(rt);
+  if (p == KL_ECUDA) return KL_ECUDA;
+  if (!rt->in_flight || (rt->kind != kServe && rt->kind != kServeBase)) return KL_ESTATE;  // the run has ended
+  if (rt->kind == kServeBase && rt->s_joined) return KL_ESTATE;
+  if (rt->kind == kServe && __atomic_load_n(&rt->sm_ctl[32], __ATOMIC_RELAXED)) return KL_ESTATE;  // stopping
+  if (rt->s_inflight >= rt->cap) return KL_EAGAIN;
+  if (rt->cfg.mem_cap_bytes && rt->s_footprint + footprint > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
+  const uint32_t seq = rt->s_tail;
+  if (seq >= 0xfffffff0u) return KL_EOVERFLOW;
+  td.index = seq;
+  td.slice = clamp_slice(rt, td.slice, td.total);
+  if (rt->kind == kServe) {
+    memcpy(&rt->sm_ring[seq & (rt->s_ring - 1u)], &td, sizeof(td));
+    __atomic_store_n(&rt->sm_ctl[0], seq + 1u, __ATOMIC_RELEASE);
+  } else {
+    const uint32_t k = seq % rt->s_nstreams;
+    cudaEvent_t e = nullptr;
+    if (!rt->s_free_ev.empty()) {
+      e = rt->s_free_ev.back();
+      rt->s_free_ev.pop_back();
+    } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      return KL_ECUDA;
+    }
+    if (native_launch_tenant(td.type, td.args, rt->side[k]) != 0 || cudaEventRecord(e, rt->side[k]) != cudaSuccess) {
+      rt->s_free_ev.push_back(e);
+      return KL_ECUDA;
+    }
+    rt->s_stream_q[k].emplace_back(seq, e);
+  }
+  ServeRec r{};
+  r.t_submit = now_ns();
+  r.footprint = footprint;
+  r.state = KL_RUNNING;
+  r.total = td.total;
+  rt->s_recs.push_back(r);
+  rt->s_tail = seq + 1u;
+  rt->s_inflight++;
+  rt->s_footprint += footprint;
+  *out = make_handle(rt->flight_id, seq);
+  return KL_OK;
 }
 
 }  // namespace
@@ -470,14 +704,18 @@ extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime*
     s = std::min<uint32_t>(std::min<uint32_t>(s, (uint32_t)occ), KL_MAX_SLOTS);
     rt->slots = s;
   }
+  // the device indexes tenants and phases modulo a power of two (a ring in
+  // serving mode); a batch run never wraps: n <= cap tenants, <= 4 cap + 16 phases
   rt->cap = cfg.max_tenants;
   rt->cap_phases = 4 * rt->cap + 16;
-  if (cudaMalloc(&rt->d_tenants, sizeof(TenantDev) * rt->cap) != cudaSuccess) goto fail_mem;
+  rt->ring_slots = pow2_at_least(rt->cap);
+  rt->phase_slots = pow2_at_least(rt->cap_phases);
+  if (cudaMalloc(&rt->d_tenants, sizeof(TenantDev) * rt->ring_slots) != cudaSuccess) goto fail_mem;
   if (cudaMalloc(&rt->d_run, sizeof(RunDev)) != cudaSuccess) goto fail_mem;
-  if (cudaMalloc(&rt->d_phases, sizeof(PhaseDev) * rt->cap_phases) != cudaSuccess) goto fail_mem;
-  if (cudaMallocHost(&rt->h_tenants, sizeof(TenantDev) * rt->cap) != cudaSuccess) goto fail_mem;
+  if (cudaMalloc(&rt->d_phases, sizeof(PhaseDev) * rt->phase_slots) != cudaSuccess) goto fail_mem;
+  if (cudaMallocHost(&rt->h_tenants, sizeof(TenantDev) * rt->ring_slots) != cudaSuccess) goto fail_mem;
   if (cudaMallocHost(&rt->h_run, sizeof(RunDev)) != cudaSuccess) goto fail_mem;
-  if (cudaMallocHost(&rt->h_phases, sizeof(PhaseDev) * rt->cap_phases) != cudaSuccess) goto fail_mem;
+  if (cudaMallocHost(&rt->h_phases, sizeof(PhaseDev) * rt->phase_slots) != cudaSuccess) goto fail_mem;
   if (cudaEventCreate(&rt->ev_start) != cudaSuccess || cudaEventCreate(&rt->ev_done) != cudaSuccess ||
       cudaEventCreate(&rt->ev_k0) != cudaSuccess || cudaEventCreate(&rt->ev_k1) != cudaSuccess ||
       cudaEventCreateWithFlags(&rt->ev_fork, cudaEventDisableTiming) != cudaSuccess)
@@ -511,6 +749,8 @@ extern "C" int kl_destroy(kl_runtime* rt) {
   int rc = KL_OK;
   {
     std::unique_lock<std::mutex> lk(rt->mu);
+    if (rt->in_flight && rt->kind == kServe) __atomic_store_n(&rt->sm_ctl[32], 1u, __ATOMIC_RELEASE);
+    if (rt->in_flight && rt->kind == kServeBase && !rt->s_joined) serve_join(rt);
     if (rt->in_flight) {
       int w = wait_flight(rt, lk, rt->cfg.device_wait_limit_ns * 4 + 1000000000ull);
       if (w == KL_ETIMEDOUT) rc = KL_ESTATE;
@@ -523,6 +763,16 @@ extern "C" int kl_destroy(kl_runtime* rt) {
   cudaFreeHost(rt->h_tenants);
   cudaFreeHost(rt->h_run);
   cudaFreeHost(rt->h_phases);
+  cudaFree(rt->sd_ring);
+  cudaFree(rt->sd_phases);
+  cudaFreeHost(rt->sh_phases);
+  cudaFreeHost(rt->sm_ring);
+  cudaFreeHost(rt->sm_ctl);
+  cudaFreeHost(rt->sm_done);
+  cudaFreeHost(rt->sm_cq);
+  for (cudaEvent_t e : rt->s_free_ev) cudaEventDestroy(e);
+  for (auto& q : rt->s_stream_q)
+    for (auto& x : q) cudaEventDestroy(x.second);
   if (rt->ev_start) cudaEventDestroy(rt->ev_start);
   if (rt->ev_done) cudaEventDestroy(rt->ev_done);
   if (rt->ev_k0) cudaEventDestroy(rt->ev_k0);
@@ -547,18 +797,21 @@ extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out
   if (d->smem_bytes != 0 && d->smem_bytes < sh.smem_bytes) return KL_EINVAL;
   if (sh.total_blocks == 0 || sh.total_blocks >= (1ull << 31)) return KL_EINVAL;
   std::lock_guard<std::mutex> lk(rt->mu);
+  TenantDev td;
+  memset(&td, 0, sizeof(td));
+  td.type = d->type;
+  td.slice = d->slice_blocks                   ? d->slice_blocks
+             : rt->prof[d->type].slice_blocks ? rt->prof[d->type].slice_blocks
+                                              : default_slice(d->type);
+  td.total = (uint32_t)sh.total_blocks;
+  td.nstages = sh.nstages;
+  memcpy(td.args, d->args, d->args_size);
+  if (rt->serve_on) return serve_publish(rt, td, d->footprint_bytes, out);
   if (rt->pending.size() >= rt->cap) return KL_EAGAIN;
   if (rt->cfg.mem_cap_bytes && rt->pending_footprint + d->footprint_bytes > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
   Pending p;
-  memset(&p.td, 0, sizeof(p.td));
-  p.td.type = d->type;
-  p.td.slice = d->slice_blocks                       ? d->slice_blocks
-                : rt->prof[d->type].slice_blocks ? rt->prof[d->type].slice_blocks
-                                                 : default_slice(d->type);
-  p.td.total = (uint32_t)sh.total_blocks;
-  p.td.nstages = sh.nstages;
+  p.td = td;
   p.td.index = (uint32_t)rt->pending.size();
-  memcpy(p.td.args, d->args, d->args_size);
   p.footprint = d->footprint_bytes;
   p.t_submit = now_ns();
   p.handle = make_handle(rt->run_id, p.td.index);
@@ -587,17 +840,15 @@ static int launch_locked(kl_runtime* rt) {
   R.n_types = KL_T_COUNT;
   R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
   R.flags = rt->cfg.flags;
+  R.serve = 0;
+  R.ring_mask = rt->ring_slots - 1;
+  R.phase_mask = rt->phase_slots - 1;
   memcpy(R.cp, rt->cp, sizeof(R.cp));
   memcpy(R.slots_a, rt->slots_a, sizeof(R.slots_a));
   memcpy(R.allowed, rt->allowed, sizeof(R.allowed));
-  // A slice never exceeds the kernel, and the queue counter (which can
-  // overshoot by one slice per CTA when a kernel runs out) stays below 2^32.
-  const uint64_t ctas = (uint64_t)rt->n_sm * rt->slots;
   for (uint32_t i = 0; i < n; ++i) {
     TenantDev td = rt->pending[i].td;
-    uint64_t sl = std::min<uint64_t>(td.slice, td.total);
-    while (sl > 1 && (uint64_t)td.total + sl * (ctas + 1) >= (1ull << 32)) sl >>= 1;
-    td.slice = (uint32_t)std::max<uint64_t>(sl, 1);
+    td.slice = clamp_slice(rt, td.slice, td.total);
     rt->h_tenants[i] = td;
   }
   PhaseDev first{};
@@ -631,6 +882,7 @@ static int launch_locked(kl_runtime* rt) {
 extern "C" int kl_launch(kl_runtime* rt) {
   if (!rt) return KL_EINVAL;
   std::lock_guard<std::mutex> lk(rt->mu);
+  if (rt->serve_on) return KL_ESTATE;
   return launch_locked(rt);
 }
 
@@ -638,6 +890,7 @@ extern "C" int kl_launch_baseline(kl_runtime* rt, int mode, uint32_t nstreams) {
   if (!rt || (mode != KL_BASE_SERIAL && mode != KL_BASE_MULTISTREAM)) return KL_EINVAL;
   if (mode == KL_BASE_MULTISTREAM && (nstreams == 0 || nstreams > 256)) return KL_EINVAL;
   std::lock_guard<std::mutex> lk(rt->mu);
+  if (rt->serve_on) return KL_ESTATE;
   if (rt->in_flight && progress(rt) == KL_EAGAIN) return KL_EAGAIN;
   const uint32_t n = (uint32_t)rt->pending.size();
   if (n == 0) return KL_OK;
@@ -688,6 +941,157 @@ extern "C" int kl_launch_baseline(kl_runtime* rt, int mode, uint32_t nstreams) {
   return KL_OK;
 }
 
+// Serving buffers, allocated at the first co-scheduled kl_serve_start: the
+// device tenant and phase rings, and the mapped host ring, control words,
+// completion records and completion queue.
+static int serve_alloc(kl_runtime* rt) {
+  if (rt->sd_ring) return KL_OK;
+  const uint32_t ring = pow2_at_least(std::max<uint64_t>(65536, 4ull * rt->cap));
+  const uint32_t nph = 65536;
+  void* p = nullptr;
+  if (cudaMalloc(&rt->sd_ring, sizeof(TenantDev) * ring) != cudaSuccess) return KL_ENOMEM;
+  if (cudaMalloc(&rt->sd_phases, sizeof(PhaseDev) * nph) != cudaSuccess) return KL_ENOMEM;
+  if (cudaMallocHost(&rt->sh_phases, sizeof(PhaseDev) * nph) != cudaSuccess) return KL_ENOMEM;
+  if (cudaHostAlloc(&p, sizeof(TenantDev) * ring, cudaHostAllocMapped) != cudaSuccess) return KL_ENOMEM;
+  rt->sm_ring = (TenantDev*)p;
+  if (cudaHostAlloc(&p, 256, cudaHostAllocMapped) != cudaSuccess) return KL_ENOMEM;
+  rt->sm_ctl = (uint32_t*)p;
+  if (cudaHostAlloc(&p, sizeof(ServeDone) * ring, cudaHostAllocMapped) != cudaSuccess) return KL_ENOMEM;
+  rt->sm_done = (ServeDone*)p;
+  if (cudaHostAlloc(&p, sizeof(unsigned long long) * ring, cudaHostAllocMapped) != cudaSuccess) return KL_ENOMEM;
+  rt->sm_cq = (unsigned long long*)p;
+  if (cudaHostGetDevicePointer((void**)&rt->sdm_ring, rt->sm_ring, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&rt->sdm_ctl, rt->sm_ctl, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&rt->sdm_done, rt->sm_done, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&rt->sdm_cq, rt->sm_cq, 0) != cudaSuccess)
+    return KL_ECUDA;
+  rt->s_ring = ring;
+  rt->s_phase_slots = nph;
+  return KL_OK;
+}
+
+extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint64_t idle_limit_ns) {
+  if (!rt) return KL_EINVAL;
+  if (mode != KL_SERVE_COSCHED && mode != KL_BASE_SERIAL && mode != KL_BASE_MULTISTREAM) return KL_EINVAL;
+  if (mode == KL_BASE_MULTISTREAM && (nstreams == 0 || nstreams > 256)) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  if (rt->serve_on) return KL_ESTATE;
+  if (rt->in_flight && progress(rt) == KL_EAGAIN) return KL_EAGAIN;
+  if (cudaSetDevice(rt->device) != cudaSuccess) return KL_ECUDA;
+  int rc = KL_OK;
+  cudaStream_t s = rt->stream;
+  if (mode == KL_SERVE_COSCHED) {
+    rc = serve_alloc(rt);
+    if (rc) return rc;
+    rc = ensure_table(rt, (1u << KL_T_COUNT) - 1u);  // arrivals may be of any type
+    if (rc) return rc;
+    memset(rt->sm_ctl, 0, 256);
+    memset(rt->sm_cq, 0, sizeof(unsigned long long) * rt->s_ring);
+    RunDev& R = *rt->h_run;
+    memset(&R, 0, sizeof(R));
+    R.slots = rt->slots;
+    R.max_phases = rt->s_phase_slots;
+    R.n_types = KL_T_COUNT;
+    R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
+    R.flags = rt->cfg.flags;
+    R.serve = 1;
+    R.ring_mask = rt->s_ring - 1u;
+    R.phase_mask = rt->s_phase_slots - 1u;
+    R.idle_limit_ns = idle_limit_ns ? idle_limit_ns : 60000000000ull;
+    R.host_ring = rt->sdm_ring;
+    R.host_ctl = rt->sdm_ctl;
+    R.host_done = rt->sdm_done;
+    R.host_cq = rt->sdm_cq;
+    memcpy(R.cp, rt->cp, sizeof(R.cp));
+    memcpy(R.slots_a, rt->slots_a, sizeof(R.slots_a));
+    memcpy(R.allowed, rt->allowed, sizeof(R.allowed));
+    PhaseDev first{};
+    first.A = kPhasePlan;
+    first.B = -1;
+    for (int f = 0; f < 4; ++f) first.fill[f] = -1;
+    rt->sh_phases[0] = first;
+    rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
+    if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
+    if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->sd_phases, rt->sh_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
+    if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
+    if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, s) != 0) rc = KL_ECUDA;
+    if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
+    if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
+    if (!rc)
+      rc = cuda_ok(cudaMemcpyAsync(rt->sh_phases, rt->sd_phases, sizeof(PhaseDev) * rt->s_phase_slots,
+                                   cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_done, s));
+    if (rc) return rc;
+    rt->kind = kServe;
+  } else {
+    const uint32_t ns = mode == KL_BASE_SERIAL ? 1u : nstreams;
+    while (rt->side.size() < ns) {
+      cudaStream_t q;
+      cudaEvent_t e;
+      if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) return KL_ECUDA;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return KL_ECUDA;
+      rt->side.push_back(q);
+      rt->side_join.push_back(e);
+    }
+    rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
+    if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
+    if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_fork, s));
+    for (uint32_t k = 0; k < ns && !rc; ++k) rc = cuda_ok(cudaStreamWaitEvent(rt->side[k], rt->ev_fork, 0));
+    if (rc) return rc;
+    rt->s_nstreams = ns;
+    rt->s_stream_q.assign(ns, {});
+    rt->s_joined = false;
+    rt->kind = kServeBase;
+  }
+  rt->serve_on = true;
+  rt->serve_mode = mode;
+  rt->in_flight = true;
+  rt->flight_id = rt->run_id++;  // kernels still pending keep their handles: they arrive first
+  rt->s_tail = rt->s_head = rt->s_inflight = 0;
+  rt->s_footprint = 0;
+  rt->s_recs.clear();
+  rt->completed.clear();
+  std::vector<Pending> early;
+  early.swap(rt->pending);
+  rt->pending_footprint = 0;
+  kl_handle h = 0;
+  for (const Pending& p : early) {
+    rc = serve_publish(rt, p.td, p.footprint, &h);
+    if (rc) return rc;
+    rt->s_recs.back().t_submit = p.t_submit;
+  }
+  return KL_OK;
+}
+
+extern "C" int kl_serve_stop(kl_runtime* rt, uint64_t timeout_ns) {
+  if (!rt) return KL_EINVAL;
+  std::unique_lock<std::mutex> lk(rt->mu);
+  if (!rt->serve_on) return KL_ESTATE;
+  int rc = KL_OK;
+  if (rt->in_flight && rt->kind == kServe) __atomic_store_n(&rt->sm_ctl[32], 1u, __ATOMIC_RELEASE);
+  if (rt->in_flight && rt->kind == kServeBase && !rt->s_joined) rc = serve_join(rt);
+  if (rc) return rc;
+  if (rt->in_flight) {
+    rc = wait_flight(rt, lk, timeout_ns);
+    if (rc == KL_ETIMEDOUT || rc == KL_ECUDA) return rc;
+  }
+  rt->serve_on = false;
+  return rt->last.error;
+}
+
+extern "C" int kl_reap(kl_runtime* rt, kl_handle* out, uint32_t cap, uint32_t* n) {
+  if (!rt || !n || (cap && !out)) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  *n = 0;
+  int p = progress(rt);
+  if (p == KL_ECUDA) return p;
+  while (*n < cap && !rt->completed.empty()) {
+    out[(*n)++] = rt->completed.front();
+    rt->completed.pop_front();
+  }
+  return KL_OK;
+}
+
 static int lookup(kl_runtime* rt, kl_handle h, kl_tenant_stats* st) {
   uint64_t run;
   uint32_t idx;
@@ -698,6 +1102,21 @@ static int lookup(kl_runtime* rt, kl_handle h, kl_tenant_stats* st) {
     memset(st, 0, sizeof(*st));
     st->state = KL_PENDING;
     st->t_submit_ns = rt->pending[idx].t_submit;
+    return KL_OK;
+  }
+  if (rt->in_flight && run == rt->flight_id && (rt->kind == kServe || rt->kind == kServeBase)) {
+    if (idx >= rt->s_recs.size()) return KL_ENOTFOUND;
+    const ServeRec& r = rt->s_recs[idx];
+    memset(st, 0, sizeof(*st));
+    st->state = (int32_t)r.state;
+    st->t_submit_ns = r.t_submit;
+    st->t_done_host_ns = r.t_done_host;
+    if (r.state == KL_DONE) {
+      st->t_start_ns = r.done.t_start;
+      st->t_end_ns = r.done.t_end;
+      st->slices = r.done.slices;
+      st->blocks = rt->kind == kServe ? r.done.blocks : r.total;
+    }
     return KL_OK;
   }
   if (rt->in_flight && run == rt->flight_id) {
@@ -732,11 +1151,20 @@ extern "C" int kl_wait(kl_runtime* rt, kl_handle h, uint64_t timeout_ns) {
   int rc = lookup(rt, h, &st);
   if (rc) return rc;
   if (st.state == KL_PENDING) return KL_ESTATE;  // not launched: waiting would never end
-  if (st.state == KL_RUNNING) {
-    rc = wait_flight(rt, lk, timeout_ns);
-    if (rc == KL_ETIMEDOUT || rc == KL_ECUDA) return rc;
+  const uint64_t t0 = now_ns();
+  for (uint32_t spins = 0; st.state == KL_RUNNING; ++spins) {
+    int p = progress(rt);
+    if (p == KL_ECUDA) return p;
     rc = lookup(rt, h, &st);
     if (rc) return rc;
+    if (st.state != KL_RUNNING) break;
+    if (now_ns() - t0 >= timeout_ns) return KL_ETIMEDOUT;
+    lk.unlock();
+    if (spins < 64)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    lk.lock();
   }
   return st.state == KL_DONE ? KL_OK : (st.error ? st.error : KL_ESTATE);
 }
@@ -744,6 +1172,7 @@ extern "C" int kl_wait(kl_runtime* rt, kl_handle h, uint64_t timeout_ns) {
 extern "C" int kl_drain(kl_runtime* rt, uint64_t timeout_ns) {
   if (!rt) return KL_EINVAL;
   std::unique_lock<std::mutex> lk(rt->mu);
+  if (rt->serve_on) return KL_ESTATE;
   int rc;
   if (rt->in_flight) {
     rc = wait_flight(rt, lk, timeout_ns);

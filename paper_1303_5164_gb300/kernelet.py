@@ -26,7 +26,7 @@ KL_T_COUNT = 10
 TYPE_NAMES = ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256",
               "escape", "bitonic", "matadd"]
 KL_RATIO_BALANCED, KL_RATIO_MAX_CP, KL_RATIO_FIXED = 0, 1, 2
-KL_BASE_SERIAL, KL_BASE_MULTISTREAM = 0, 1
+KL_BASE_SERIAL, KL_BASE_MULTISTREAM, KL_SERVE_COSCHED = 0, 1, 2
 KL_CFG_BACKFILL = 1
 KL_CFG_FILL_TYPES = 2
 
@@ -118,7 +118,8 @@ class kl_phase(C.Structure):
 
 class kl_tenant_stats(C.Structure):
     _fields_ = [("state", I32), ("error", I32), ("t_submit_ns", U64), ("t_start_ns", U64),
-                ("t_end_ns", U64), ("t_launch_ns", U64), ("slices", U32), ("blocks", U32)]
+                ("t_end_ns", U64), ("t_launch_ns", U64), ("slices", U32), ("blocks", U32),
+                ("t_done_host_ns", U64)]
 
 
 class kl_run_stats(C.Structure):
@@ -145,6 +146,9 @@ SIGNATURES = [
     ("kl_tenant_shape_of", C.c_int, [U32, P, U32, C.POINTER(kl_tenant_shape)]),
     ("kl_submit", C.c_int, [P, C.POINTER(kl_kernel_desc), C.POINTER(U64)]),
     ("kl_launch", C.c_int, [P]),
+    ("kl_serve_start", C.c_int, [P, C.c_int, U32, U64]),
+    ("kl_serve_stop", C.c_int, [P, U64]),
+    ("kl_reap", C.c_int, [P, C.POINTER(U64), U32, C.POINTER(U32)]),
     ("kl_launch_baseline", C.c_int, [P, C.c_int, U32]),
     ("kl_poll", C.c_int, [P, U64, C.POINTER(C.c_int)]),
     ("kl_wait", C.c_int, [P, U64, U64]),
@@ -315,6 +319,29 @@ class Runtime:
 
     def launch(self):
         check(lib().kl_launch(self._h), "kl_launch")
+
+    def serve_start(self, mode: int = KL_SERVE_COSCHED, nstreams: int = 0, idle_limit_ns: int = 0):
+        check(lib().kl_serve_start(self._h, mode, nstreams, idle_limit_ns), "kl_serve_start")
+
+    def reap(self, cap: int = 4096):
+        """Handles completed since the last call (serving mode)."""
+        buf = (U64 * cap)()
+        n = U32()
+        check(lib().kl_reap(self._h, buf, cap, C.byref(n)), "kl_reap")
+        return list(buf[: n.value])
+
+    def serve_stop(self, timeout_ns: int = 30_000_000_000) -> int:
+        return lib().kl_serve_stop(self._h, timeout_ns)
+
+    def try_submit(self, type_: int, args, slice_blocks: int = 0, footprint: int = 0):
+        """Like submit(), but returns None instead of raising on KL_EAGAIN."""
+        d = make_desc(type_, args, slice_blocks, footprint)
+        h = U64()
+        rc = lib().kl_submit(self._h, C.byref(d), C.byref(h))
+        if rc == KL_EAGAIN:
+            return None
+        check(rc, "kl_submit")
+        return h.value
 
     def launch_baseline(self, mode: int, nstreams: int = 32):
         check(lib().kl_launch_baseline(self._h, mode, nstreams), "kl_launch_baseline")

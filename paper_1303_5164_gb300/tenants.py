@@ -61,6 +61,17 @@ class Tenant:
     def shape(self):
         return K.tenant_shape(self.type, self.args)
 
+    def replica(self) -> "Tenant":
+        """Another request on the same inputs: shared input buffers, fresh
+        output buffers (output buffer names equal the argument fields)."""
+        torch = _torch()
+        b = dict(self.bufs)
+        args = type(self.args).from_buffer_copy(self.args)
+        for k in self.outputs:
+            b[k] = torch.empty_like(self.bufs[k])
+            setattr(args, k, _ptr(b[k]))
+        return Tenant(self.name, self.type, args, b, list(self.outputs), self.footprint)
+
 
 def make(name: str, inp: dict, device="cuda") -> Tenant:
     """Device tenant from the seeded host inputs of workloads.gen.gen_<name>."""
