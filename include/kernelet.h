@@ -82,7 +82,8 @@ typedef enum {
     KL_T_ESCAPE = 7,        /* escape-time iteration count per pixel, uint32       */
     KL_T_BITONIC = 8,       /* ascending bitonic sort of 2^log2n uint32 keys        */
     KL_T_MATADD = 9,        /* c = a + b on an n x n matrix, 16x16 blocks (Section 4.1 example) */
-    KL_T_COUNT = 10
+    KL_T_GEMM_BF16 = 10,    /* C = A B^T, BF16 inputs, FP32 accumulate, tensor cores */
+    KL_T_COUNT = 11
 } kl_tenant_type;
 
 /* ----------------------------------------------------------- tenant arguments
@@ -163,6 +164,16 @@ typedef struct {            /* KL_T_MATADD: 16x16-thread blocks, (n/16)^2 grid *
     uint32_t pad;
 } kl_args_matadd;
 
+typedef struct {            /* KL_T_GEMM_BF16: one 128x64 tile of C per block  */
+    const uint16_t* A;      /* [M][K] bfloat16 bits, 16B, K multiple of 8      */
+    const uint16_t* Bt;     /* [N][K] bfloat16 bits (B stored column-major)    */
+    float* C;               /* [M][N] 16B, N multiple of 4                     */
+    const void* tmaps;      /* device copy of the 256 bytes written by
+                               kl_gemm_bf16_tensor_maps (64B aligned); caller
+                               owned, alive until the kernel is DONE           */
+    uint32_t M, N, K, pad;
+} kl_args_gemm_bf16;
+
 /* Launch shape of a tenant as a plain kernel would use it (Section 2.2: a
  * kernel is k thread blocks). Multi-stage tenants (histogram, bitonic sort)
  * are a chain of grids; stage s may start only when stage s-1 has finished. */
@@ -204,6 +215,15 @@ typedef enum {
 #define KL_CFG_FILL_TYPES 2u /* backfill tries the next pending kernels of the two
                                types the co-schedule runs before any other
                                pending kernel; default on */
+#define KL_CFG_SERVE_TC 8u   /* serving runs use the co-scheduler build that can
+                               run KL_T_GEMM_BF16 (tensor cores); without it a
+                               serving run refuses that type (KL_EINVAL). Batch
+                               runs pick the build from the kernels they hold. */
+#define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
+                               dependent grids) are pending outside the current
+                               co-schedule, the last slot of every SM takes their
+                               slices first, so their stage barriers overlap
+                               other work instead of forming the end of the run */
 
 typedef struct {
     int32_t device;                 /* CUDA ordinal (default 0)                     */
@@ -216,7 +236,8 @@ typedef struct {
     uint64_t mem_cap_bytes;         /* admission cap on summed footprints (0 = none) */
     double alpha_p, alpha_m;        /* pruning thresholds; negative = no pruning    */
     uint32_t flags;                 /* KL_CFG_* bits                                */
-    uint32_t reserved;
+    uint32_t chain_slots;           /* KL_CFG_CHAIN_LANE: slots per SM (the last ones)
+                                       that serve multi-stage kernels first; 0 = 1 */
 } kl_config;
 
 /* Model inputs for one tenant type (Table 1 parameters, measured by profiling
@@ -305,6 +326,15 @@ int kl_create(const kl_config* cfg, void* cuda_stream, kl_runtime** out);
 /* Wait for in-flight work (up to the device wait limit), free everything.
  * KL_ESTATE if a run could not be retired. */
 int kl_destroy(kl_runtime* rt);
+
+/* Tensor maps (two CUtensorMap, 128 bytes each: A then Bt) that the
+ * KL_T_GEMM_BF16 tenant's TMA loads read: 2-D tiles of 64 K-elements x 128
+ * rows of A and x 64 rows of Bt, 128-byte swizzle, zero fill outside the
+ * matrix. Written to out_host (256 bytes, host memory); the caller copies them
+ * to device memory and passes that address as kl_args_gemm_bf16.tmaps. Needs
+ * the CUDA driver (no device work). KL_EINVAL on misaligned pointers, K not a
+ * multiple of 8, or a zero size; KL_ECUDA when the driver refuses the map. */
+int kl_gemm_bf16_tensor_maps(const kl_args_gemm_bf16* args, void* out_host);
 
 /* Launch shape of a tenant (no device work). */
 int kl_tenant_shape_of(uint32_t type, const void* args, uint32_t args_size, kl_tenant_shape* out);

@@ -101,6 +101,33 @@ def gemm_f32_sample(A, B, ii, jj):
     return out
 
 
+def bf16_to_f64(bits):
+    """Value of bfloat16 bit patterns: the upper half of a binary32 word."""
+    b = np.ascontiguousarray(bits, dtype=np.uint16)
+    return (b.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+
+
+def gemm_bf16(A, Bt):
+    """C = A B^T of bfloat16 inputs, by definition in binary64 (a product of
+    two bfloat16 values is exact in binary64; the sum is one library matmul).
+    Also returns sum_k |a_ik b_jk|, the scale of the accumulation error bound."""
+    a = bf16_to_f64(A)
+    b = bf16_to_f64(Bt)
+    return a @ b.T, np.abs(a) @ np.abs(b).T
+
+
+def gemm_bf16_sample(A, Bt, ii, jj):
+    """Entries (ii[t], jj[t]) of gemm_bf16, each a binary64 dot product."""
+    c = np.empty(len(ii))
+    s = np.empty(len(ii))
+    for t, (i, j) in enumerate(zip(ii, jj)):
+        a = bf16_to_f64(A[i])
+        b = bf16_to_f64(Bt[j])
+        c[t] = float(np.dot(a, b))
+        s[t] = float(np.dot(np.abs(a), np.abs(b)))
+    return c, s
+
+
 def spmv_csr(rowptr, col, val, x):
     n = len(rowptr) - 1
     y32 = np.empty(n, np.float32)

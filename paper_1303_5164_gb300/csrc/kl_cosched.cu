@@ -86,6 +86,7 @@ struct CtaCtl {
   int32_t trigger;
   int32_t wait_failed;
   uint32_t from, to;   // dispatcher: kernels to copy in
+  uint32_t mine;       // dispatcher: this CTA claimed the re-plan
 };
 
 __device__ __forceinline__ void set_error(RunDev* R, int32_t code, uint32_t info) {
@@ -127,55 +128,124 @@ __device__ __forceinline__ int try_pull(TenantDev* T, const RunDev* R, int32_t t
   return kPulled;
 }
 
-// FindCoSchedule on the device (Algorithm 1, procedure), warp 0 of one CTA.
-// Pending = kernels with blocks not yet handed out, among sequence numbers
-// [scan_lo, end) (end = kernels submitted; in serving mode, copied in). For
-// every pair of pending kernels CP depends only on their types, so the best
-// pair of a type pair is its two lowest sequence numbers; the winner is the
-// largest CP among unpruned type pairs (all pairs when every one is pruned),
-// ties to the smallest (i, j). One pending kernel runs alone on every slot;
-// none ends a batch run, or idles a serving run until the next arrival.
-__device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, int32_t trigger) {
-  const int lane = threadIdx.x & 31;
-  int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
-#pragma unroll
-  for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
-  uint32_t npend = 0;
-  unsigned long long pmask = 0ull;
+// Per-warp partial results of the pending-set scan, in the re-planning CTA's
+// dynamic shared memory (free between tenant blocks).
+struct ScanPart {
+  uint32_t npend;
+  int32_t first;
+  unsigned long long pmask;
+  uint32_t nlow, nms;
   int32_t lowp[6];
-  uint32_t nlow = 0;
-  int32_t lowms = -1;  // lowest pending kernel with more than one stage
-  const uint32_t lo = ld_relaxed(&R->scan_lo);
-  const uint32_t hi = R->serve ? ld_acquire(&R->intake) : R->n_tenants;
-  int32_t first_pending = -1;
-  for (uint32_t base = lo; base < hi; base += 32) {
-    const uint32_t i = base + lane;
-    bool pend = false, multi = false;
-    uint32_t ty = 0;
-    if (i < hi) {
-      const TenantDev& d = tenant(T, R, i);
-      ty = d.type;
-      pend = ld_relaxed(&d.next) < d.total;
-      multi = d.nstages > 1;
-    }
-    const uint32_t pb = __ballot_sync(0xffffffffu, pend);
-    npend += __popc(pb);
-    if (pb && first_pending < 0) first_pending = (int32_t)(base + __ffs(pb) - 1);
-    if (base < 64) pmask |= (unsigned long long)pb << base;
-    for (uint32_t m = pb; m && nlow < 6; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
-    const uint32_t msb = __ballot_sync(0xffffffffu, pend && multi);
-    if (msb && lowms < 0) lowms = (int32_t)(base + __ffs(msb) - 1);
+  int32_t lowms[4];
+  int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
+};
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kPlanScratch = sizeof(ScanPart) * kWarps + 16;
+static_assert(kPlanScratch <= tn::kMinCtaSmem, "re-plan scratch fits the smallest dynamic shared memory");
+
+// FindCoSchedule on the device (Algorithm 1, procedure), all threads of one
+// CTA. Pending = kernels with blocks not yet handed out, among sequence
+// numbers [scan_lo, end) (end = kernels submitted; in serving mode, copied
+// in); each warp scans a contiguous eighth of that range and thread 0 merges
+// the eight partial results in order. For every pair of pending kernels CP
+// depends only on their types, so the best pair of a type pair is its two
+// lowest sequence numbers; the winner is the largest CP among unpruned type
+// pairs (all pairs when every one is pruned), ties to the smallest (i, j). One
+// pending kernel runs alone on every slot; none ends a batch run, or idles a
+// serving run until the next arrival.
+__device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, int32_t trigger, char* smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ScanPart* parts = reinterpret_cast<ScanPart*>(smem);
+  uint32_t* bounds = reinterpret_cast<uint32_t*>(parts + kWarps);
+  if (threadIdx.x == 0) {
+    bounds[0] = ld_relaxed(&R->scan_lo);
+    bounds[1] = R->serve ? ld_acquire(&R->intake) : R->n_tenants;
+  }
+  __syncthreads();
+  const uint32_t lo = bounds[0], hi = bounds[1];
+  {
+    int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
 #pragma unroll
-    for (int t = 0; t < KL_T_COUNT; ++t) {
-      uint32_t m = __ballot_sync(0xffffffffu, pend && ty == (uint32_t)t);
-      if (m && low1[t] < 0) {
-        low1[t] = (int32_t)(base + __ffs(m) - 1);
-        m &= m - 1;
+    for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
+    uint32_t npend = 0, nlow = 0, nms = 0;
+    unsigned long long pmask = 0ull;
+    int32_t lowp[6], lowms[4];
+    int32_t first_pending = -1;
+    const uint32_t nchunk = hi > lo ? (hi - lo + 31u) / 32u : 0u;
+    const uint32_t cpw = (nchunk + kWarps - 1) / kWarps;
+    const uint32_t b0 = lo + 32u * min(nchunk, (uint32_t)warp * cpw);
+    const uint32_t b1 = lo + 32u * min(nchunk, (uint32_t)(warp + 1) * cpw);
+    for (uint32_t base = b0; base < b1; base += 32) {
+      const uint32_t i = base + lane;
+      bool pend = false, multi = false;
+      uint32_t ty = 0;
+      if (i < hi) {
+        const TenantDev& d = tenant(T, R, i);
+        // static fields through L2: in serving mode the slot may have been refilled
+        ty = __ldcg(&d.type);
+        pend = ld_relaxed(&d.next) < __ldcg(&d.total);
+        multi = __ldcg(&d.nstages) > 1u;
       }
-      if (m && low2[t] < 0) low2[t] = (int32_t)(base + __ffs(m) - 1);
+      const uint32_t pb = __ballot_sync(0xffffffffu, pend);
+      npend += __popc(pb);
+      if (pb && first_pending < 0) first_pending = (int32_t)(base + __ffs(pb) - 1);
+      if (base < 64) pmask |= (unsigned long long)pb << base;
+      for (uint32_t m = pb; m && nlow < 6; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
+      const uint32_t msb = __ballot_sync(0xffffffffu, pend && multi);
+      for (uint32_t m = msb; m && nms < 4; m &= m - 1) lowms[nms++] = (int32_t)(base + __ffs(m) - 1);
+#pragma unroll
+      for (int t = 0; t < KL_T_COUNT; ++t) {
+        uint32_t m = __ballot_sync(0xffffffffu, pend && ty == (uint32_t)t);
+        if (m && low1[t] < 0) {
+          low1[t] = (int32_t)(base + __ffs(m) - 1);
+          m &= m - 1;
+        }
+        if (m && low2[t] < 0) low2[t] = (int32_t)(base + __ffs(m) - 1);
+      }
+    }
+    if (lane == 0) {
+      ScanPart& q = parts[warp];
+      q.npend = npend;
+      q.first = first_pending;
+      q.pmask = pmask;
+      q.nlow = nlow;
+      q.nms = nms;
+      for (uint32_t f = 0; f < nlow; ++f) q.lowp[f] = lowp[f];
+      for (uint32_t f = 0; f < nms; ++f) q.lowms[f] = lowms[f];
+#pragma unroll
+      for (int t = 0; t < KL_T_COUNT; ++t) {
+        q.low1[t] = low1[t];
+        q.low2[t] = low2[t];
+      }
     }
   }
-  if (lane != 0) return;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // merge in warp order (warp w scanned lower sequence numbers than warp w+1)
+  int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
+  for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
+  uint32_t npend = 0, nlow = 0, nms = 0;
+  unsigned long long pmask = 0ull;
+  int32_t lowp[6], lowms[4];
+  int32_t first_pending = -1;
+  for (int w = 0; w < kWarps; ++w) {
+    const ScanPart& q = parts[w];
+    npend += q.npend;
+    pmask |= q.pmask;
+    if (first_pending < 0) first_pending = q.first;
+    for (uint32_t f = 0; f < q.nlow && nlow < 6; ++f) lowp[nlow++] = q.lowp[f];
+    for (uint32_t f = 0; f < q.nms && nms < 4; ++f) lowms[nms++] = q.lowms[f];
+    for (int t = 0; t < KL_T_COUNT; ++t) {
+      const int32_t c[2] = {q.low1[t], q.low2[t]};
+      for (int k = 0; k < 2; ++k) {
+        if (c[k] < 0) break;
+        if (low1[t] < 0)
+          low1[t] = c[k];
+        else if (low2[t] < 0)
+          low2[t] = c[k];
+      }
+    }
+  }
   // kernels below the first pending one are all handed out: skip them next time
   st_release(&R->scan_lo, first_pending >= 0 ? (uint32_t)first_pending : hi);
   PhaseDev ph;
@@ -248,9 +318,15 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
       if (sb >= 0 && sb != ph.A && (c == 0 || sb != ph.fill[0])) ph.fill[c++] = sb;
     }
   }
-  if (lowms >= 0 && c < 4 && lowms != ph.A && lowms != ph.B && (c == 0 || lowms != ph.fill[0]) &&
-      (c < 2 || lowms != ph.fill[1]))
-    ph.fill[c++] = lowms;
+  // chain lane: the two lowest multi-stage kernels outside the pair
+  ph.chain[0] = ph.chain[1] = -1;
+  {
+    uint32_t nc = 0;
+    for (uint32_t f = 0; f < nms && nc < 2; ++f)
+      if (lowms[f] != ph.A && lowms[f] != ph.B) ph.chain[nc++] = lowms[f];
+  }
+  if (ph.chain[0] >= 0 && c < 4 && (c == 0 || ph.chain[0] != ph.fill[0]) && (c < 2 || ph.chain[0] != ph.fill[1]))
+    ph.fill[c++] = ph.chain[0];
   for (uint32_t f = 0; f < nlow && c < 4; ++f) {
     bool dup = lowp[f] == ph.A || lowp[f] == ph.B;
     for (uint32_t q = 0; q < c; ++q) dup |= lowp[f] == ph.fill[q];
@@ -300,7 +376,7 @@ __device__ __forceinline__ void complete_tenant(TenantDev& d, RunDev* R) {
 }
 
 // Serving mode, CTA 0: copy arrivals in, re-plan, end the run on request.
-__device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl) {
+__device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl, char* smem) {
   const int tid = threadIdx.x;
   unsigned long long last_arrival = gtimer();
   unsigned long long stop_since = 0;
@@ -329,6 +405,7 @@ __device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl) {
             PhaseDev* e = phase(P, R, seq + 1);
             e->A = kPhaseEnd;
             e->B = -1;
+            e->chain[0] = e->chain[1] = -1;
             e->intake_seen = intake;
             e->t = now;
             __threadfence();
@@ -355,29 +432,32 @@ __device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl) {
           dst[tid] = ld_volatile64(src + tid);
         }
         __threadfence();
-        __syncwarp();
-        // re-plan on arrival (Algorithm 1); if a re-plan is already running,
-        // the workers see intake > intake_seen and ask for another
-        uint32_t seq = 0, mine = 0;
-        if (tid == 0) {
-          st_release(&R->intake, ctl.to);
-          seq = ld_acquire(&R->phase_seq);
-          mine = ld_relaxed(&R->phase_claim) == seq && atomicCAS(&R->phase_claim, seq, seq + 1) == seq;
-        }
-        mine = __shfl_sync(0xffffffffu, mine, 0);
-        seq = __shfl_sync(0xffffffffu, seq, 0);
-        if (mine) replan(T, R, P, seq, -1);
       }
+      __syncthreads();
+      // re-plan on arrival (Algorithm 1); if a re-plan is already running,
+      // the workers see intake > intake_seen and ask for another
+      if (tid == 0) {
+        st_release(&R->intake, ctl.to);
+        const uint32_t seq = ld_acquire(&R->phase_seq);
+        ctl.seq = seq;
+        ctl.mine = ld_relaxed(&R->phase_claim) == seq && atomicCAS(&R->phase_claim, seq, seq + 1) == seq;
+      }
+      __syncthreads();
+      if (ctl.mine) replan(T, R, P, ctl.seq, -1, smem);
     }
     __syncthreads();
   }
 }
 
+// TC = true: the build that can run the tensor-core BF16 GEMM tenant (used
+// only for runs that contain one; see run_block).
+template <bool TC>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev* __restrict__ T, RunDev* __restrict__ R,
                                                                       PhaseDev* __restrict__ P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaCtl ctl;
   __shared__ uint32_t s_slot;
+  __shared__ uint32_t s_tmem;  // TMEM columns of this CTA (BF16 GEMM blocks)
   const int tid = threadIdx.x;
   if (tid == 0) {
     const uint32_t sm = smid() & (kMaxSM - 1);
@@ -386,8 +466,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     atomicCAS(&R->t_launch, 0ull, gtimer());
   }
   __syncthreads();
+  const tn::BlockCtx tcx{&s_tmem, &R->error, R->wait_limit_ns};
+  if constexpr (TC) tn::acquire_tmem(tcx);
   if (R->serve && blockIdx.x == 0) {
-    dispatcher(T, R, P, ctl);
+    dispatcher(T, R, P, ctl, smem);
+    if constexpr (TC) tn::release_tmem(tcx);
     if (tid == 0) atomicAdd(&R->ctas_done, 1u);
     return;
   }
@@ -425,6 +508,22 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
             ctl.trigger = -1;
           }
           idle = ph.A == kPhaseIdle;
+          // chain lane: the last slot of every SM serves pending multi-stage
+          // kernels first (their stage barriers then overlap the pair's work)
+          if (ph.A >= 0 && ctl.action == kActWait && (R->flags & KL_CFG_CHAIN_LANE) && slot + R->chain_slots >= S) {
+            for (int f = 0; f < 2; ++f) {
+              const int32_t c = __ldcg(&pp->chain[f]);
+              if (c < 0) break;
+              uint32_t g0 = 0, g1 = 0;
+              if (try_pull(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
+                ctl.action = kActRun;
+                ctl.tenant = c;
+                ctl.g0 = g0;
+                ctl.g1 = g1;
+                break;
+              }
+            }
+          }
           if (ph.A >= 0 && ctl.action == kActWait) {
             const bool mine_is_b = ph.B >= 0 && slot >= ph.slots_a;
             const int32_t t1 = mine_is_b ? ph.B : ph.A;
@@ -509,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     const uint32_t action = ctl.action;
     if (action == kActExit) break;
     if (action == kActReplan) {
-      if (tid < 32) replan(T, R, P, ctl.seq, ctl.trigger);
+      replan(T, R, P, ctl.seq, ctl.trigger, smem);
     } else if (action == kActRun) {
       TenantDev& d = tenant(T, R, (uint32_t)ctl.tenant);
       const uint32_t type = d.type;
@@ -537,8 +636,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
           if (ctl.wait_failed) break;
         }
         const uint32_t ge = min(g1, st.end);
+        const tn::BlockCtx cx{&s_tmem, &R->error, limit};
         for (uint32_t b = g; b < ge; ++b) {
-          tn::run_block(type, d.args, st, b, smem);
+          tn::run_block<TC>(type, d.args, st, b, smem, cx);
           __syncthreads();  // shared memory is reused by the next block
         }
         if (tid == 0) {
@@ -553,24 +653,32 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     }
     __syncthreads();
   }
+  if constexpr (TC) tn::release_tmem(tcx);
   if (tid == 0) atomicAdd(&R->ctas_done, 1u);
 }
 
 // ------------------------------------------------------------------ host side
 
-int cosched_occupancy(int* ctas_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(cosched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <bool TC>
+static int occupancy_of(int* ctas_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(cosched_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tn::kMaxTenantSmem);
   if (e != cudaSuccess) return -1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, cosched_kernel, kThreads,
-                                                    tn::kMaxTenantSmem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, cosched_kernel<TC>, kThreads, tn::kMaxTenantSmem);
   return e == cudaSuccess ? 0 : -1;
 }
 
-int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots,
-                   cudaStream_t stream) {
+int cosched_occupancy(int* ctas_per_sm, bool tensor_cores) {
+  return tensor_cores ? occupancy_of<true>(ctas_per_sm) : occupancy_of<false>(ctas_per_sm);
+}
+
+int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
+                   bool tensor_cores, cudaStream_t stream) {
   dim3 grid(n_sm * slots), block(kThreads);
-  cosched_kernel<<<grid, block, tn::kMaxTenantSmem, stream>>>(T, R, P);
+  if (tensor_cores)
+    cosched_kernel<true><<<grid, block, smem_bytes, stream>>>(T, R, P);
+  else
+    cosched_kernel<false><<<grid, block, smem_bytes, stream>>>(T, R, P);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

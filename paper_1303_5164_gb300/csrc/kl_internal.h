@@ -48,8 +48,9 @@ struct PhaseDev {
   uint32_t prev_done_b;
   uint32_t intake_seen;        // kernels known to the device when the phase was chosen
   uint32_t pad2;
+  int32_t chain[2];            // lowest pending multi-stage kernels outside A, B (chain lane)
 };
-static_assert(sizeof(PhaseDev) == 88, "PhaseDev layout");
+static_assert(sizeof(PhaseDev) == 96, "PhaseDev layout");
 
 // Serving mode: per-kernel completion record in mapped host memory, written
 // by the device before the kernel's entry in the completion queue.
@@ -76,6 +77,8 @@ struct alignas(128) RunDev {
   uint32_t n_types;
   uint32_t flags;              // kl_config.flags
   uint32_t serve;              // 1: serving mode (tenant ring, dispatcher CTA 0)
+  uint32_t chain_slots;        // chain lane: the last chain_slots slots of every SM
+  uint32_t pad_s;
   unsigned long long wait_limit_ns;
   uint32_t ring_mask;          // tenant slots - 1 (power of two); tenant seq -> slot
   uint32_t phase_mask;         // phase slots - 1 (power of two)

@@ -15,11 +15,18 @@ struct ArgsBlob {
   alignas(16) unsigned char b[KL_MAX_ARGS_BYTES];
 };
 
+// Device-side errors of plain launches (a BF16 GEMM wait that ran out).
+__device__ int g_native_error;
+
 template <int TYPE>
 __global__ void __launch_bounds__(kThreads) native_kernel(ArgsBlob args, uint32_t stage) {
   extern __shared__ __align__(16) char smem[];
+  __shared__ uint32_t s_tmem;
   const tn::Stage st{stage, 0u, 0u};
-  tn::run_block(TYPE, args.b, st, blockIdx.x, smem);
+  const tn::BlockCtx cx{&s_tmem, &g_native_error, 2000000000ull};
+  if constexpr (TYPE == KL_T_GEMM_BF16) tn::acquire_tmem(cx);
+  tn::run_block<TYPE == KL_T_GEMM_BF16>(TYPE, args.b, st, blockIdx.x, smem, cx);
+  if constexpr (TYPE == KL_T_GEMM_BF16) tn::release_tmem(cx);
 }
 
 template <int TYPE>
@@ -53,6 +60,7 @@ int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s) {
       case KL_T_ESCAPE: e = launch_one<KL_T_ESCAPE>(args, st, nb, s); break;
       case KL_T_BITONIC: e = launch_one<KL_T_BITONIC>(args, st, nb, s); break;
       case KL_T_MATADD: e = launch_one<KL_T_MATADD>(args, st, nb, s); break;
+      case KL_T_GEMM_BF16: e = launch_one<KL_T_GEMM_BF16>(args, st, nb, s); break;
       default: return -1;
     }
     if (e != cudaSuccess) return -1;

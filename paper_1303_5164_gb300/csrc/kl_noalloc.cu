@@ -24,8 +24,9 @@
 #include "tenants.cuh"
 
 namespace kl {
-int cosched_occupancy(int* ctas_per_sm);
-int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, cudaStream_t stream);
+int cosched_occupancy(int* ctas_per_sm, bool tensor_cores);
+int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
+                   bool tensor_cores, cudaStream_t stream);
 
 namespace {
 
@@ -81,7 +82,8 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
   PhaseDev* dP = reinterpret_cast<PhaseDev*>(base + kPhaseOff);
 
   int occ = 0, nsm = 0;
-  if (cosched_occupancy(&occ) != 0 || occ < 1) return KL_ECUDA;
+  int occ_tc = 0;  // also raises the tensor-core build's dynamic shared memory limit
+  if (cosched_occupancy(&occ, false) != 0 || occ < 1 || cosched_occupancy(&occ_tc, true) != 0) return KL_ECUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return KL_ECUDA;
   const uint32_t S = (uint32_t)(occ < KL_MAX_SLOTS ? occ : KL_MAX_SLOTS);
   const uint32_t n_sm = (uint32_t)(nsm < kMaxSM ? nsm : kMaxSM);
@@ -117,6 +119,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
   R.max_phases = 4 * n + 16;
   R.n_types = KL_T_COUNT;
   R.flags = KL_CFG_BACKFILL;
+  R.chain_slots = 1;
   R.ring_mask = kMaxT - 1;
   R.phase_mask = kPhaseSlots - 1;
   R.wait_limit_ns = wait_limit_ns ? wait_limit_ns : 2000000000ull;
@@ -130,13 +133,16 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
   img.ph0.A = -2;
   img.ph0.B = -1;
   for (int f = 0; f < 4; ++f) img.ph0.fill[f] = -1;
+  img.ph0.chain[0] = img.ph0.chain[1] = -1;
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (cudaMemcpyAsync(dT, img.t, sizeof(TenantDev) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(dR, &img.run, sizeof(RunDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(dP, &img.ph0, sizeof(PhaseDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return KL_ECUDA;
-  if (cosched_launch(dT, dR, dP, n_sm, S, s) != 0) return KL_ECUDA;
+  bool tc = false;
+  for (uint32_t i = 0; i < n; ++i) tc |= descs[i].type == KL_T_GEMM_BF16;
+  if (cosched_launch(dT, dR, dP, n_sm, S, tn::kMaxTenantSmem, tc, s) != 0) return KL_ECUDA;
   if (cudaMemcpyAsync(img.t, dT, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&img.run, dR, sizeof(RunDev), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return KL_ECUDA;

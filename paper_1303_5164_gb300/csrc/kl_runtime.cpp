@@ -8,6 +8,8 @@
 // before; here the CP / balanced-split table per type pair is cached the same
 // way); FindCoSchedule and the "repeat the co-schedule until a kernel runs out"
 // loop run on the device (kl_cosched.cu).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,8 +28,9 @@
 #include "tenants.cuh"
 
 namespace kl {
-int cosched_occupancy(int* ctas_per_sm);
-int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, cudaStream_t stream);
+int cosched_occupancy(int* ctas_per_sm, bool tensor_cores);
+int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
+                   bool tensor_cores, cudaStream_t stream);
 int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s);
 namespace model {
 int pair(const kl_model_params& g, const kl_profile& pa, const kl_profile& pb, uint32_t slots, int states,
@@ -59,6 +62,7 @@ size_t args_size_of(uint32_t type) {
     case KL_T_ESCAPE: return sizeof(kl_args_escape);
     case KL_T_BITONIC: return sizeof(kl_args_bitonic);
     case KL_T_MATADD: return sizeof(kl_args_matadd);
+    case KL_T_GEMM_BF16: return sizeof(kl_args_gemm_bf16);
     default: return 0;
   }
 }
@@ -119,6 +123,13 @@ int validate_args(uint32_t type, const void* a) {
       if (!m->a || !m->b || !m->c || m->n == 0 || m->n % 16) return KL_EINVAL;
       return KL_OK;
     }
+    case KL_T_GEMM_BF16: {
+      const kl_args_gemm_bf16* g = (const kl_args_gemm_bf16*)a;
+      if (!g->A || !g->Bt || !g->C || !g->tmaps || g->M == 0 || g->N == 0 || g->K == 0) return KL_EINVAL;
+      if (g->K % 8 || g->N % 4 || !a16(g->A) || !a16(g->Bt) || !a16(g->C) || ((uintptr_t)g->tmaps & 63u))
+        return KL_EINVAL;
+      return KL_OK;
+    }
     default: return KL_EINVAL;
   }
 }
@@ -138,6 +149,7 @@ uint32_t default_slice(uint32_t type) {
     case KL_T_ESCAPE: return 8;
     case KL_T_BITONIC: return 2;
     case KL_T_MATADD: return 8;
+    case KL_T_GEMM_BF16: return 1;
     default: return 1;
   }
 }
@@ -162,6 +174,7 @@ kl_profile builtin_profile(uint32_t type) {
     case KL_T_ESCAPE: p.R_m = 0.001; p.f_u = 0.0; p.L0 = 700; p.I_block = 8 * 1500; p.PUR = 0.70; p.MUR = 0.01; break;
     case KL_T_BITONIC: p.R_m = 0.10; p.f_u = 0.0; p.L0 = 500; p.I_block = 8 * 400; p.PUR = 0.30; p.MUR = 0.30; break;
     case KL_T_MATADD: p.R_m = 0.25; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 12; p.PUR = 0.05; p.MUR = 0.70; break;
+    case KL_T_GEMM_BF16: p.R_m = 0.02; p.f_u = 0.0; p.L0 = 700; p.I_block = 8 * 200; p.PUR = 0.10; p.MUR = 0.10; break;
     default: p.valid = 0; break;
   }
   return p;
@@ -582,6 +595,7 @@ int serve_publish(kl_runtime* rt, TenantDev td, uint64_t footprint, kl_handle* o
   if (!rt->in_flight || (rt->kind != kServe && rt->kind != kServeBase)) return KL_ESTATE;  // the run has ended
   if (rt->kind == kServeBase && rt->s_joined) return KL_ESTATE;
   if (rt->kind == kServe && __atomic_load_n(&rt->sm_ctl[32], __ATOMIC_RELAXED)) return KL_ESTATE;  // stopping
+  if (rt->kind == kServe && td.type == KL_T_GEMM_BF16 && !(rt->cfg.flags & KL_CFG_SERVE_TC)) return KL_EINVAL;
   if (rt->s_inflight >= rt->cap) return KL_EAGAIN;
   if (rt->cfg.mem_cap_bytes && rt->s_footprint + footprint > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
   const uint32_t seq = rt->s_tail;
@@ -675,6 +689,42 @@ extern "C" int kl_tenant_shape_of(uint32_t type, const void* args, uint32_t args
   return KL_OK;
 }
 
+extern "C" int kl_gemm_bf16_tensor_maps(const kl_args_gemm_bf16* a, void* out_host) {
+  if (!a || !out_host) return KL_EINVAL;
+  if (!a->A || !a->Bt || a->M == 0 || a->N == 0 || a->K == 0 || a->K % 8 || !a16(a->A) || !a16(a->Bt))
+    return KL_EINVAL;
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+          q != cudaDriverEntryPointSuccess || !fn)
+        return KL_ECUDA;
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+  }
+  CUtensorMap maps[2];
+  const void* base[2] = {a->A, a->Bt};
+  const uint32_t rows[2] = {a->M, a->N};
+  const uint32_t box_rows[2] = {(uint32_t)tn::kBfBM, (uint32_t)tn::kBfBN};
+  for (int i = 0; i < 2; ++i) {
+    const cuuint64_t dims[2] = {a->K, rows[i]};           // innermost first: K, then rows
+    const cuuint64_t strides[1] = {(cuuint64_t)a->K * 2};  // bytes between rows
+    const cuuint32_t box[2] = {(cuuint32_t)tn::kBfBK, box_rows[i]};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base[i]), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return KL_ECUDA;
+  }
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  memcpy(out_host, maps, sizeof(maps));
+  return KL_OK;
+}
+
 extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime** out) {
   if (!out) return KL_EINVAL;
   *out = nullptr;
@@ -698,7 +748,10 @@ extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime*
   rt->n_sm = (uint32_t)std::min(v, kMaxSM);
   {
     int occ = 0;
-    if (cosched_occupancy(&occ) != 0 || occ < 1) goto fail_cuda;
+    // the tensor-core build reaches the same residency: its CTAs give up the
+    // TMEM allocation permit right after allocating (see acquire_tmem)
+    int occ_tc = 0;  // also raises the tensor-core build's dynamic shared memory limit
+    if (cosched_occupancy(&occ, false) != 0 || occ < 1 || cosched_occupancy(&occ_tc, true) != 0) goto fail_cuda;
     rt->occupancy = (uint32_t)occ;
     uint32_t s = cfg.slots_per_sm ? cfg.slots_per_sm : (uint32_t)occ;
     s = std::min<uint32_t>(std::min<uint32_t>(s, (uint32_t)occ), KL_MAX_SLOTS);
@@ -827,8 +880,11 @@ static int launch_locked(kl_runtime* rt) {
   const uint32_t n = (uint32_t)rt->pending.size();
   if (n == 0) return KL_OK;
   if (cudaSetDevice(rt->device) != cudaSuccess) return KL_ECUDA;
-  uint32_t mask = 0;
-  for (const Pending& p : rt->pending) mask |= 1u << p.td.type;
+  uint32_t mask = 0, smem = tn::kMinCtaSmem;
+  for (const Pending& p : rt->pending) {
+    mask |= 1u << p.td.type;
+    smem = std::max(smem, tn::smem_bytes(p.td.type));  // dynamic shared memory of this run's CTAs
+  }
   int rc = ensure_table(rt, mask);
   if (rc) return rc;
   // device image: run state, tenants, the "plan first" phase
@@ -841,6 +897,7 @@ static int launch_locked(kl_runtime* rt) {
   R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
   R.flags = rt->cfg.flags;
   R.serve = 0;
+  R.chain_slots = std::max(1u, std::min(rt->cfg.chain_slots, rt->slots - 1));
   R.ring_mask = rt->ring_slots - 1;
   R.phase_mask = rt->phase_slots - 1;
   memcpy(R.cp, rt->cp, sizeof(R.cp));
@@ -855,6 +912,7 @@ static int launch_locked(kl_runtime* rt) {
   first.A = -2;
   first.B = -1;
   for (int f = 0; f < 4; ++f) first.fill[f] = -1;
+  first.chain[0] = first.chain[1] = -1;
   rt->h_phases[0] = first;
   cudaStream_t s = rt->stream;
   rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
@@ -862,7 +920,9 @@ static int launch_locked(kl_runtime* rt) {
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_phases, rt->h_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
-  if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, rt->slots, s) != 0) rc = KL_ECUDA;
+  const bool tc = (mask >> KL_T_GEMM_BF16) & 1u;
+  if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, rt->slots, smem, tc, s) != 0)
+    rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_tenants, rt->d_tenants, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
@@ -995,6 +1055,7 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
     R.flags = rt->cfg.flags;
     R.serve = 1;
+    R.chain_slots = std::max(1u, std::min(rt->cfg.chain_slots, rt->slots - 1));
     R.ring_mask = rt->s_ring - 1u;
     R.phase_mask = rt->s_phase_slots - 1u;
     R.idle_limit_ns = idle_limit_ns ? idle_limit_ns : 60000000000ull;
@@ -1009,12 +1070,15 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     first.A = kPhasePlan;
     first.B = -1;
     for (int f = 0; f < 4; ++f) first.fill[f] = -1;
+    first.chain[0] = first.chain[1] = -1;
     rt->sh_phases[0] = first;
     rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->sd_phases, rt->sh_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
     if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
-    if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, s) != 0) rc = KL_ECUDA;
+    if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, tn::kMaxTenantSmem,
+                              (rt->cfg.flags & KL_CFG_SERVE_TC) != 0, s) != 0)
+      rc = KL_ECUDA;
     if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
     if (!rc)

@@ -48,6 +48,14 @@ constexpr int kTriadPerBlock = 4096;
 constexpr int kHistBytesPerBlock = 32768;
 constexpr int kEscapePerBlock = 256;
 constexpr int kBitonicTileLog2 = 12;  // 4096 keys per tile
+// BF16 tensor-core GEMM: 128x64 tile of C per block, K in steps of 64 (one
+// 128-byte swizzle row per operand row), two pipeline stages
+constexpr int kBfBM = 128, kBfBN = 64, kBfBK = 64;
+constexpr uint32_t kBfStageA = kBfBM * kBfBK * 2u;      // 16 KB
+constexpr uint32_t kBfStageB = kBfBN * kBfBK * 2u;      // 8 KB
+constexpr uint32_t kBfStage = kBfStageA + kBfStageB;
+constexpr uint32_t kBfSmem = 1024u + 2u * kBfStage + 64u;  // alignment slack, stages, barriers
+constexpr uint32_t kBfTmemCols = 64;                       // FP32 accumulator: 128 lanes x 64 columns
 
 __host__ __device__ inline uint32_t bitonic_tile_log2(uint32_t L) {
   return L < (uint32_t)kBitonicTileLog2 ? L : (uint32_t)kBitonicTileLog2;
@@ -92,6 +100,10 @@ __host__ __device__ inline uint32_t stage_blocks(uint32_t type, const void* a, u
       uint32_t t = ((const kl_args_matadd*)a)->n / 16;
       return t * t;
     }
+    case KL_T_GEMM_BF16: {
+      const kl_args_gemm_bf16* g = (const kl_args_gemm_bf16*)a;
+      return cdiv64(g->M, kBfBM) * cdiv64(g->N, kBfBN);
+    }
     default: return 0;
   }
 }
@@ -124,13 +136,26 @@ __host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
     case KL_T_SPMV_CSR: return 256u;                                              // long-row list
     case KL_T_HIST256: return 256u * 32u * 4u;                                    // 32 KB
     case KL_T_BITONIC: return ((1u << kBitonicTileLog2) + (1u << (kBitonicTileLog2 - 5))) * 4u;  // padded tile
+    case KL_T_GEMM_BF16: return kBfSmem;                                          // 49.1 KB
     default: return 0;
   }
 }
-constexpr uint32_t kMaxTenantSmem = 256u * 32u * 4u;  // largest of the above (histogram)
+constexpr uint32_t kMaxTenantSmem = kBfSmem;  // largest of the above (BF16 GEMM)
+constexpr uint32_t kMinCtaSmem = 2048;         // co-scheduler CTAs always have this much (re-plan scratch)
+static_assert(256u * 32u * 4u <= kMaxTenantSmem, "smem bound");
 static_assert(2u * (kGemmBK * kGemmAStride + kGemmBK * kGemmBN) * 4u <= kMaxTenantSmem, "smem bound");
 
 #ifdef __CUDACC__
+
+// Per-CTA context a tenant body may need besides its arguments: the shared
+// word holding the CTA's TMEM address (kernels built with the tensor-core
+// tenant), the word that records a device-side error, and the bound on any
+// wait.
+struct BlockCtx {
+  uint32_t* tmem;
+  int* err;
+  unsigned long long limit_ns;
+};
 
 // ------------------------------------------------------------------ helpers
 
@@ -855,6 +880,228 @@ __device__ __forceinline__ void matadd_block(const kl_args_matadd& a, uint32_t v
   a.c[i] = __fadd_rn(a.a[i], a.b[i]);
 }
 
+// ------------------------------------------------------------------ BF16 GEMM on tensor cores
+// C[M][N] = sum_k A[m][k] * Bt[n][k], A and Bt bfloat16 (both K-major), FP32
+// accumulation in tensor memory. Per block (one 128x64 tile of C): thread 0
+// issues the TMA loads of 128x64 (A) and 64x64 (Bt) K-slices into a two-stage
+// ring of 128-byte-swizzled shared memory and the tcgen05.mma instructions
+// (M=128, N=64, K=16 each, four per K-slice); tcgen05.commit signals an
+// mbarrier when a stage's MMAs have read their operands, which frees the stage
+// for the next TMA load. After the last K-slice all eight warps read the
+// accumulator with tcgen05.ld (warp w: lanes 32(w mod 4).., columns 32(w/4)..)
+// and store their rows of C. Rows and columns outside C are zero-filled by
+// the TMA unit and not stored. The caller allocates the TMEM columns when the
+// CTA starts (acquire_tmem, BlockCtx::tmem) and frees them at its end. Every
+// mbarrier wait is bounded by BlockCtx::limit_ns; a wait that runs out
+// records KL_EDEVICE_TIMEOUT in *BlockCtx::err and the block stores nothing.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long tn_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// false when the phase did not complete within limit_ns
+static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = tn_gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if (tn_gtimer() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand whose 128-byte rows follow
+// the 128-byte swizzle, groups of 8 rows 1024 bytes apart (stride offset);
+// the leading offset is unused in this layout; version 1; swizzle mode 2.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// bfloat16 (bits 7-9 = 1, 10-12 = 1), both K-major, N/8 at bit 17, M/16 at 24.
+constexpr uint32_t kBfIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBfBN >> 3) << 17) |
+                              ((uint32_t)(kBfBM >> 4) << 24);
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(kBfIdesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// whole warp
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 16 consecutive FP32 columns of this warp's 32 lanes; one lane = one row
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float4 (&v)[4]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    v[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
+                       __uint_as_float(r[4 * q + 3]));
+}
+
+static __device__ void gemm_bf16_block(const kl_args_gemm_bf16& a, uint32_t vb, char* smem, const BlockCtx& cx) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t tiles_n = cdiv64(a.N, kBfBN);
+  const uint32_t m0 = (vb / tiles_n) * kBfBM, n0 = (vb % tiles_n) * kBfBN;
+  const uint32_t kt = cdiv64(a.K, kBfBK);
+  const uint32_t base = (smem_u32(smem) + 1023u) & ~1023u;  // swizzled tiles need 1024-byte alignment
+  const uint32_t full0 = base + 2u * kBfStage;               // TMA -> MMA, per stage
+  const uint32_t freed0 = full0 + 16u;                       // MMA done reading, per stage
+  const uint32_t accb = full0 + 32u;                         // all MMAs of the tile done
+  volatile uint32_t* flag = reinterpret_cast<volatile uint32_t*>(smem + (full0 + 40u - smem_u32(smem)));
+  const uint32_t tmem = *cx.tmem;  // allocated by acquire_tmem when the CTA started
+  if (tid == 0) {
+    mbar_init(full0, 1u);
+    mbar_init(full0 + 8u, 1u);
+    mbar_init(freed0, 1u);
+    mbar_init(freed0 + 8u, 1u);
+    mbar_init(accb, 1u);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // earlier blocks wrote this shared memory through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t ok = 1u;
+    const char* tmA = static_cast<const char*>(a.tmaps);
+    const char* tmB = tmA + 128;
+    for (uint32_t s = 0; s < 2u && s < kt; ++s) {
+      mbar_expect_tx(full0 + 8u * s, kBfStage);
+      tma_load_2d(base + s * kBfStage, tmA, (int32_t)(s * kBfBK), (int32_t)m0, full0 + 8u * s);
+      tma_load_2d(base + s * kBfStage + kBfStageA, tmB, (int32_t)(s * kBfBK), (int32_t)n0, full0 + 8u * s);
+    }
+    for (uint32_t i = 0; i < kt; ++i) {
+      const uint32_t s = i & 1u, ph = (i >> 1) & 1u;
+      if (!mbar_wait(full0 + 8u * s, ph, cx.limit_ns)) {
+        ok = 0u;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = base + s * kBfStage, sb = sa + kBfStageA;
+#pragma unroll
+      for (uint32_t k = 0; k < (uint32_t)kBfBK / 16u; ++k)
+        umma_bf16(tmem, umma_desc_sw128(sa + 32u * k), umma_desc_sw128(sb + 32u * k), (i | k) != 0u);
+      umma_commit(freed0 + 8u * s);
+      if (i + 2u < kt) {
+        if (!mbar_wait(freed0 + 8u * s, ph, cx.limit_ns)) {
+          ok = 0u;
+          break;
+        }
+        mbar_expect_tx(full0 + 8u * s, kBfStage);
+        tma_load_2d(sa, tmA, (int32_t)((i + 2u) * kBfBK), (int32_t)m0, full0 + 8u * s);
+        tma_load_2d(sb, tmB, (int32_t)((i + 2u) * kBfBK), (int32_t)n0, full0 + 8u * s);
+      }
+    }
+    if (ok) umma_commit(accb);  // arrives once every MMA issued above has completed
+    // the stage-free signals of the last two K-slices were never waited for:
+    // collect them so no arrival lands after the barriers are invalidated
+    for (uint32_t i = kt > 2u ? kt - 2u : 0u; ok && i < kt; ++i)
+      if (!mbar_wait(freed0 + 8u * (i & 1u), (i >> 1) & 1u, cx.limit_ns)) ok = 0u;
+    *flag = ok;
+  }
+  __syncthreads();
+  bool ok = *flag != 0u;
+  if (ok) ok = mbar_wait(accb, 0u, cx.limit_ns);
+  tc_fence_after();
+  if (ok) {
+    const uint32_t q = (uint32_t)warp & 3u, h = (uint32_t)warp >> 2;
+    const uint32_t row = m0 + 32u * q + (uint32_t)lane;
+    const uint32_t c0 = n0 + 32u * h;
+#pragma unroll
+    for (uint32_t half = 0; half < 2u; ++half) {
+      float4 v[4];
+      tmem_ld16(tmem + ((32u * q) << 16) + 32u * h + 16u * half, v);
+      if (row < a.M) {
+        float4* dst = reinterpret_cast<float4*>(a.C + (uint64_t)row * a.N + c0 + 16u * half);
+#pragma unroll
+        for (uint32_t j = 0; j < 4u; ++j)
+          if (c0 + 16u * half + 4u * j < a.N) dst[j] = v[j];
+      }
+    }
+  } else if (lane == 0) {
+    atomicCAS(cx.err, 0, (int)KL_EDEVICE_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    mbar_inval(full0);
+    mbar_inval(full0 + 8u);
+    mbar_inval(freed0);
+    mbar_inval(freed0 + 8u);
+    mbar_inval(accb);
+  }
+  __syncthreads();
+}
+
+// CTA start (all threads): allocate the accumulator's TMEM columns, then give
+// up the allocation permit at once. The hardware keeps further CTAs of a
+// TMEM-allocating kernel off an SM while a resident CTA still holds its
+// permit (measured on GB300: one CTA per SM at a time without the relinquish,
+// four with it); at most four CTAs x 64 columns of the SM's 512 are ever
+// allocated, so the allocation never waits.
+__device__ __forceinline__ void acquire_tmem(const BlockCtx& cx) {
+  if ((threadIdx.x >> 5) == 0) {
+    tmem_alloc(smem_u32(cx.tmem), kBfTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// CTA exit (all threads): free the columns acquire_tmem allocated.
+__device__ __forceinline__ void release_tmem(const BlockCtx& cx) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(*cx.tmem, kBfTmemCols);
+}
+
 // ------------------------------------------------------------------ dispatch
 // Runs cumulative block g (of stage st) of a tenant. All 256 threads call it.
 
@@ -863,8 +1110,12 @@ __device__ __forceinline__ A load_args(const void* p) {
   return *reinterpret_cast<const A*>(p);
 }
 
+// TC: whether this caller is built with the tensor-core tenant. Any tcgen05
+// instruction in a kernel makes the CUDA occupancy calculator allow one CTA
+// per SM, so kernels that never run the BF16 GEMM are built without it.
+template <bool TC>
 __device__ __forceinline__ void run_block(uint32_t type, const void* args, const Stage& st, uint32_t g,
-                                          char* smem) {
+                                          char* smem, const BlockCtx& cx) {
   const uint32_t vb = g - st.begin;
   switch (type) {
     case KL_T_GATHER: gather_block(load_args<kl_args_gather>(args), vb); break;
@@ -877,6 +1128,9 @@ __device__ __forceinline__ void run_block(uint32_t type, const void* args, const
     case KL_T_ESCAPE: escape_block(load_args<kl_args_escape>(args), vb); break;
     case KL_T_BITONIC: bitonic_block(load_args<kl_args_bitonic>(args), st.s, vb, smem); break;
     case KL_T_MATADD: matadd_block(load_args<kl_args_matadd>(args), vb); break;
+    case KL_T_GEMM_BF16:
+      if constexpr (TC) gemm_bf16_block(load_args<kl_args_gemm_bf16>(args), vb, smem, cx);
+      break;
     default: break;
   }
 }

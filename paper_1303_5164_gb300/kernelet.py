@@ -21,14 +21,16 @@ KL_OK, KL_EINVAL, KL_ENOMEM, KL_EAGAIN, KL_ETIMEDOUT, KL_ECUDA, KL_EDEVICE_TIMEO
 KL_PENDING, KL_RUNNING, KL_DONE, KL_ERROR = 0, 1, 2, 3
 
 (KL_T_GATHER, KL_T_BLACKSCHOLES, KL_T_GEMM_F32, KL_T_SPMV_CSR, KL_T_PCHASE, KL_T_TRIAD,
- KL_T_HIST256, KL_T_ESCAPE, KL_T_BITONIC, KL_T_MATADD) = range(10)
-KL_T_COUNT = 10
+ KL_T_HIST256, KL_T_ESCAPE, KL_T_BITONIC, KL_T_MATADD, KL_T_GEMM_BF16) = range(11)
+KL_T_COUNT = 11
 TYPE_NAMES = ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256",
-              "escape", "bitonic", "matadd"]
+              "escape", "bitonic", "matadd", "gemm_bf16"]
 KL_RATIO_BALANCED, KL_RATIO_MAX_CP, KL_RATIO_FIXED = 0, 1, 2
 KL_BASE_SERIAL, KL_BASE_MULTISTREAM, KL_SERVE_COSCHED = 0, 1, 2
 KL_CFG_BACKFILL = 1
 KL_CFG_FILL_TYPES = 2
+KL_CFG_CHAIN_LANE = 4
+KL_CFG_SERVE_TC = 8
 
 P = C.c_void_p
 U32, U64, I32, F32, F64 = C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
@@ -76,9 +78,13 @@ class kl_args_matadd(C.Structure):
     _fields_ = [("a", P), ("b", P), ("c", P), ("n", U32), ("pad", U32)]
 
 
+class kl_args_gemm_bf16(C.Structure):
+    _fields_ = [("A", P), ("Bt", P), ("C", P), ("tmaps", P), ("M", U32), ("N", U32), ("K", U32), ("pad", U32)]
+
+
 ARGS_TYPES = [kl_args_gather, kl_args_blackscholes, kl_args_gemm_f32, kl_args_spmv_csr,
               kl_args_pchase, kl_args_triad, kl_args_hist256, kl_args_escape, kl_args_bitonic,
-              kl_args_matadd]
+              kl_args_matadd, kl_args_gemm_bf16]
 
 
 class kl_tenant_shape(C.Structure):
@@ -96,7 +102,7 @@ class kl_config(C.Structure):
     _fields_ = [("device", I32), ("slots_per_sm", U32), ("max_tenants", U32), ("model_states", U32),
                 ("ratio_policy", U32), ("fixed_slots_a", U32), ("device_wait_limit_ns", U64),
                 ("mem_cap_bytes", U64), ("alpha_p", F64), ("alpha_m", F64), ("flags", U32),
-                ("reserved", U32)]
+                ("chain_slots", U32)]
 
 
 class kl_profile(C.Structure):
@@ -144,6 +150,7 @@ SIGNATURES = [
     ("kl_create", C.c_int, [C.POINTER(kl_config), P, C.POINTER(P)]),
     ("kl_destroy", C.c_int, [P]),
     ("kl_tenant_shape_of", C.c_int, [U32, P, U32, C.POINTER(kl_tenant_shape)]),
+    ("kl_gemm_bf16_tensor_maps", C.c_int, [C.POINTER(kl_args_gemm_bf16), P]),
     ("kl_submit", C.c_int, [P, C.POINTER(kl_kernel_desc), C.POINTER(U64)]),
     ("kl_launch", C.c_int, [P]),
     ("kl_serve_start", C.c_int, [P, C.c_int, U32, U64]),

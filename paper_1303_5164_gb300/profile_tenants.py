@@ -27,9 +27,14 @@ if ROOT not in sys.path:
 
 
 def scaled_sizes(name, scale):
-    from paper_1303_5164_gb300.tenants import SIZES_MIX
-    s = dict(SIZES_MIX[name])
+    from paper_1303_5164_gb300.tenants import SIZES_ALL
+    s = dict(SIZES_ALL[name])
     if scale == 1.0:
+        return s
+    if name == "gemm_bf16":
+        m = max(128, int(4096 * scale ** (1 / 3)) // 128 * 128)
+        return dict(M=m, N=m, K=m)
+    if name in ("gather", "matadd"):
         return s
     if name == "gemm_f32":
         m = max(64, int(1024 * scale ** (1 / 3)) // 64 * 64)
@@ -55,10 +60,10 @@ METRICS = ",".join([
 
 TYPE_OF_KERNEL = {f"native_kernel<{i}>": n for i, n in enumerate(
     ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256", "escape", "bitonic",
-     "matadd"])}
+     "matadd", "gemm_bf16"])}
 
 # working sets at or under half of L2 see the L2 latency, larger ones DRAM's
-L2_RESIDENT = {"gemm_f32", "bitonic", "pchase"}
+L2_RESIDENT = {"gemm_f32", "bitonic", "pchase", "gather", "matadd", "gemm_bf16"}
 
 
 def latency_probe(out_path: str):

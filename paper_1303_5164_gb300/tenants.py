@@ -129,6 +129,16 @@ def make(name: str, inp: dict, device="cuda") -> Tenant:
         b["out"] = _empty(inp["n"], torch.int32, device)
         args = K.kl_args_bitonic(_ptr(b["in"]), _ptr(b["out"]), inp["log2n"], 0)
         outs = ["out"]
+    elif name == "gemm_bf16":
+        b["A"] = _dev(inp["A"].view(np.int16), device)
+        b["Bt"] = _dev(inp["Bt"].view(np.int16), device)
+        b["C"] = _empty((inp["M"], inp["N"]), torch.float32, device)
+        args = K.kl_args_gemm_bf16(_ptr(b["A"]), _ptr(b["Bt"]), _ptr(b["C"]), None, inp["M"], inp["N"], inp["K"], 0)
+        maps = (C.c_ubyte * 256)()
+        K.check(K.lib().kl_gemm_bf16_tensor_maps(C.byref(args), maps), "kl_gemm_bf16_tensor_maps")
+        b["tmaps"] = torch.frombuffer(bytearray(bytes(maps)), dtype=torch.uint8).to(device)
+        args.tmaps = _ptr(b["tmaps"])
+        outs = ["C"]
     elif name == "matadd":
         b["a"], b["b"] = _dev(inp["a"], device), _dev(inp["b"], device)
         b["c"] = _empty((inp["n"], inp["n"]), torch.float32, device)
@@ -153,3 +163,7 @@ SIZES_MIX = {
     "bitonic": dict(log2n=22),
 }
 MIX_TYPES = ["gemm_f32", "spmv_csr", "blackscholes", "pchase", "triad", "hist256", "escape", "bitonic"]
+# the other types at the sizes they are profiled and validated at: the
+# two-tenant pair's gather, the MatrixAdd example, the 4096^3 tensor-core GEMM
+SIZES_OTHER = {"gather": dict(n=1 << 20), "matadd": dict(n=256), "gemm_bf16": dict(M=4096, N=4096, K=4096)}
+SIZES_ALL = {**SIZES_MIX, **SIZES_OTHER}

@@ -9,8 +9,9 @@ over the phase's cycles on all SMs. The model's numbers come from the
 runtime's own model with the measured per-type profiles.
 
 The two-tenant case (Black-Scholes 65,536 options + int32 gather 2^20, each
-in 4 slices) is also run at fixed slot ratios 1:3, 1:1 and 3:1 and against
-the same two kernels as plain launches on 2 streams.
+in 4 slices) is repeated 1000 times inside one persistent launch at fixed slot
+ratios 1:3, 1:1 and 3:1 and at the model's split, and against the same 2000
+kernels as plain launches on 2 streams.
 
     python -m paper_1303_5164_gb300.validate_pairs --out pairs.json
 """
@@ -125,61 +126,69 @@ def run(out_path, reps=3):
             "cp_predicted": pr["cp"][sa - 1], "cp_measured": cp_meas, "phase_us": dur, "kernel_us": ker}
         print("pair", a, b, json.dumps(res["pairs"][f"{a}+{b}"]), flush=True)
 
-    # the two-tenant case at fixed ratios, and on two streams
+    # the two-tenant case (configs: Black-Scholes 65,536 + gather 2^20, 4 slices
+    # each) repeated 1000 times inside ONE persistent launch, at slot ratios
+    # 1:3, 1:1, 3:1 and at the model's balanced split; against the same 2000
+    # kernels as plain launches on 2 streams. Per-pair time = run time / 1000;
+    # measured cIPC of each kernel = its blocks x instructions per block over
+    # the run's cycles on all SMs.
+    n_pairs = 1000
     bs = T.make("blackscholes", gen.gen_blackscholes(1, 0, 65536))
     ga = T.make("gather", gen.gen_gather(1, 1, 1 << 20))
-    tens["bs65k"], tens["gather1m"] = bs, ga
-    slices = [bs.shape().total_blocks // 4, ga.shape().total_blocks // 4]
-    c1 = {}
+    bss = [bs] + [bs.replica() for _ in range(n_pairs - 1)]
+    gas = [ga] + [ga.replica() for _ in range(n_pairs - 1)]
+    sl = [bs.shape().total_blocks // 4, ga.shape().total_blocks // 4]
+    ib_bs, ib_ga = profs[bs.type].I_block, profs[ga.type].I_block
+    c1 = {"pairs_per_launch": n_pairs, "slices": sl}
 
-    def lifetime_ipc(names, policy, fixed, sl):
-        # four slices per kernel end the first phase at once (every slice is
-        # handed out immediately), so the rate is taken over each kernel's life
+    def c1_run(policy, fixed):
         c2 = K.config_default()
-        c2.slots_per_sm, c2.ratio_policy, c2.fixed_slots_a = S, policy, fixed
+        c2.slots_per_sm, c2.ratio_policy, c2.fixed_slots_a, c2.max_tenants = S, policy, fixed, 4096
         r2 = K.Runtime(c2)
         r2.set_model_params(mp)
         r2.set_profiles(profs)
         best = None
         for _ in range(reps):
-            hs = [r2.submit(tens[nm].type, tens[nm].args, slice_blocks=x) for nm, x in zip(names, sl)]
+            for b_, g_ in zip(bss, gas):
+                r2.submit(b_.type, b_.args, slice_blocks=sl[0])
+                r2.submit(g_.type, g_.args, slice_blocks=sl[1])
             r2.launch()
             assert r2.drain() == 0
             ker = r2.run_stats().kernel_ns / 1e3
-            ipc = []
-            for nm, h in zip(names, hs):
-                st = r2.stats(h)
-                cyc = (st.t_end_ns - st.t_start_ns) * 1e-9 * mp.f_sm_hz
-                ipc.append(st.blocks * profs[tens[nm].type].I_block / (cyc * mp.n_sm) if cyc > 0 else None)
-            if best is None or ker < best[1]:
-                best = (ipc, ker)
+            if best is None or ker < best[0]:
+                ph = r2.phases()
+                split = ph[1].slots_a if len(ph) > 1 else None
+                best = (ker, split)
         r2.close()
-        return best
+        ker, split = best
+        cyc = ker * 1e-6 * mp.f_sm_hz * mp.n_sm
+        ipc = [n_pairs * 256 * ib_bs / cyc if ib_bs else None, n_pairs * 4096 * ib_ga / cyc if ib_ga else None]
+        return ker, split, ipc
 
     for sa in (1, 2, 3):
-        (ca, cb), ker = lifetime_ipc(["bs65k", "gather1m"], K.KL_RATIO_FIXED, sa, slices)
-        dur = None
+        ker, split, ipc = c1_run(K.KL_RATIO_FIXED, sa)
         pr = K.model_pair(mp, profs[bs.type], profs[ga.type], S, 3, K.KL_RATIO_FIXED, sa)
-        c1[f"{sa}:{S - sa}"] = {"kernel_us": ker, "cipc_measured": [ca, cb],
+        c1[f"{sa}:{S - sa}"] = {"per_pair_us": ker / n_pairs, "run_us": ker, "cipc_measured": ipc,
                                 "cipc_predicted": [pr["cipc_a"][sa - 1], pr["cipc_b"][sa - 1]],
                                 "cp_predicted": pr["cp"][sa - 1], "dT_predicted": pr["dT"][sa - 1]}
         print("c1", sa, c1[f"{sa}:{S - sa}"], flush=True)
-    r2 = K.Runtime()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ker, split, ipc = c1_run(K.KL_RATIO_BALANCED, 2)
+    c1["balanced"] = {"slots_a": split, "per_pair_us": ker / n_pairs, "run_us": ker, "cipc_measured": ipc}
+    print("c1 balanced", c1["balanced"], flush=True)
+    r2 = K.Runtime(K.config_default())
     times = []
-    for _ in range(reps + 1):
-        r2.submit(bs.type, bs.args)
-        r2.submit(ga.type, ga.args)
-        torch.cuda.synchronize()
-        e0.record()
+    for _ in range(reps):
+        for b_, g_ in zip(bss, gas):
+            r2.submit(b_.type, b_.args)
+            r2.submit(g_.type, g_.args)
         r2.launch_baseline(K.KL_BASE_MULTISTREAM, 2)
-        r2.drain()
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) * 1e3)
-    c1["two_streams_us"] = min(times)
+        assert r2.drain() == 0
+        times.append(r2.run_stats().kernel_ns / 1e3)
+    c1["two_streams_per_pair_us"] = min(times) / n_pairs
     res["c1_pair"] = c1
     r2.close()
+    del bss, gas
+    torch.cuda.empty_cache()
 
     errs = [abs(v["ipc_sum_measured"] - v["ipc_sum_predicted"]) for v in res["pairs"].values()]
     per = [abs(m - p) for v in res["pairs"].values() for m, p in zip(v["cipc_measured"], v["cipc_predicted"])

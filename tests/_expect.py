@@ -34,7 +34,19 @@ def expected(name: str, inp: dict) -> dict:
         return {"out": OT.sort_u32(inp["data"])}
     if name == "matadd":
         return {"c": OT.matadd(inp["a"], inp["b"])}
+    if name == "gemm_bf16":
+        c64, cabs = OT.gemm_bf16(inp["A"], inp["Bt"])
+        return {"_C64": c64, "_Cabs": cabs}
     raise ValueError(name)
+
+
+def gemm_bf16_bound(K, cabs):
+    """|C_gpu - C_exact| <= K * 2^-23 * sum_k |a b|: the products of bfloat16
+    values are exact in binary32, and each of the at most K binary32 additions
+    of the accumulation (whatever order and grouping the tensor cores use, and
+    whether they round to nearest or truncate) errs by less than one ulp of a
+    partial sum, itself at most sum_k |a b|."""
+    return K * 2.0 ** -23 * cabs
 
 
 SPMV_LONG = 128
@@ -63,6 +75,13 @@ def same_bits(a, b) -> bool:
 
 def check(name: str, inp: dict, got: dict, exp: dict):
     """Raises AssertionError with a short reason when `got` misses the bar."""
+    if name == "gemm_bf16":
+        c = got["C"].astype(np.float64).reshape(exp["_C64"].shape)
+        err = np.abs(c - exp["_C64"])
+        bound = gemm_bf16_bound(inp["K"], exp["_Cabs"])
+        bad = np.argwhere(err > bound)
+        assert len(bad) == 0, f"gemm_bf16 entries over bound: {bad[:5].tolist()} err {err[tuple(bad[:5].T)]}"
+        return
     if name == "spmv_csr":
         y = got["y"].astype(np.float64)
         bound = spmv_bound(inp["rowptr"], exp["_asum"])

@@ -22,6 +22,8 @@ CASES = {
     "escape": dict(width=300, height=170, max_iter=64),
     "bitonic": dict(log2n=14),
     "matadd": dict(n=256),
+    # 2 x 3 tiles of 128 x 64 with ragged M and N, 3 K-slices of 64 with a ragged 8
+    "gemm_bf16": dict(M=200, N=132, K=136),
 }
 
 
@@ -193,4 +195,47 @@ def test_mix_alone_equals_in_mix_and_decisions_match_oracle(K, T):
         else:
             assert (cs.bA, cs.bB) == (p.slots_a, p.slots_b)
             assert abs(cs.cp - p.cp) < 1e-9 * max(1.0, abs(cs.cp))
+    rt.close()
+
+
+def test_gemm_bf16_full_size_sampled(K, T):
+    # 4096^3 (the resource-heavy workload's tensor-core GEMM): 512 sampled
+    # entries, tile corners included, against binary64 dot products
+    from oracle import tenants as OT
+    inp = gen.gen_gemm_bf16(5, 0, 4096, 4096, 4096)
+    rt = _runtime(K)
+    got = _run_alone(K, rt, T.make("gemm_bf16", inp))["C"]
+    rng = np.random.default_rng(0)
+    ii = np.concatenate([[0, 127, 128, 4095, 4095, 2047], rng.integers(0, 4096, 506)])
+    jj = np.concatenate([[0, 63, 64, 4095, 0, 2048], rng.integers(0, 4096, 506)])
+    c, sabs = OT.gemm_bf16_sample(inp["A"], inp["Bt"], ii, jj)
+    err = np.abs(got[ii, jj].astype(np.float64) - c)
+    assert np.all(err <= X.gemm_bf16_bound(4096, sabs)), err.max()
+    rt.close()
+
+
+def test_tensor_core_build_coschedules_bf16_with_others(K, T):
+    # a run holding a BF16 GEMM uses the co-scheduler build with the tensor-core
+    # tenant; it keeps 4 slots per SM and pairs the GEMM with other kernels
+    items = [("gemm_bf16", dict(M=1024, N=512, K=1024)), ("blackscholes", dict(n=300000)),
+             ("triad", dict(n=1 << 22)), ("pchase", dict(N=1 << 20, nchasers=8192, hops=128)),
+             ("gemm_bf16", dict(M=256, N=256, K=2048))]
+    inps = [(nm, gen.gen_tenant(nm, 12, i, **sz)) for i, (nm, sz) in enumerate(items)]
+    rt = _runtime(K, slots_per_sm=4)
+    tens = [T.make(nm, x) for nm, x in inps]
+    hs = [rt.submit(t.type, t.args) for t in tens]
+    assert rt.drain() == 0
+    assert rt.run_stats().slots_per_sm == 4
+    ph = rt.phases()
+    pairs = [p for p in ph if p.A >= 0 and p.B >= 0]
+    assert pairs and all(p.slots_a + p.slots_b == 4 for p in pairs)
+    assert any(0 in (p.A, p.B) or 4 in (p.A, p.B) for p in pairs)
+    got = [t.fetch() for t in tens]
+    for (nm, x), g, h in zip(inps, got, hs):
+        assert rt.poll(h) == K.KL_DONE
+        X.check(nm, x, g, X.expected(nm, x))
+    for t, g in zip(tens, got):
+        alone = _run_alone(K, rt, t)
+        for k in g:
+            assert X.same_bits(alone[k], g[k]), (t.name, k)
     rt.close()

@@ -227,3 +227,53 @@ def test_matadd_and_sliced_invariance(oracle_tenants):
     for r0 in rows:
         oracle_tenants.escape(48, 40, 64, e["x0"], e["y0"], e["dx"], e["dy"], r0, r0 + 1, oe)
     assert np.array_equal(oe, full_e)
+
+
+# ---------------------------------------------------------------- BF16 GEMM (C = A B^T)
+
+def test_bf16_bits_round_to_nearest_even():
+    from workloads.gen import bf16_bits
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.0, 1.0 + 2 ** -7 + 2 ** -8], np.float32)
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: to the even one (1.0);
+    # 1 + 2^-7 + 2^-8 lies halfway between mantissas 1 (odd) and 2: to 2
+    assert bf16_bits(x).tolist() == [0x3F80, 0x3F80, 0x3F81, 0xC000, 0x3F82]
+
+
+def test_bf16_decode_known_values(oracle_tenants):
+    OT = oracle_tenants
+    v = OT.bf16_to_f64(np.array([0x3F80, 0xC000, 0x3F81, 0x0000, 0x4049], np.uint16))
+    assert v.tolist() == [1.0, -2.0, 1.0078125, 0.0, 3.140625]
+
+
+def _bf16_of_ints(a):
+    from workloads.gen import bf16_bits
+    return bf16_bits(np.asarray(a, np.float32))
+
+
+def test_gemm_bf16_small_integers_exact_and_orientation(oracle_tenants):
+    OT = oracle_tenants
+    rng = np.random.default_rng(11)
+    A = rng.integers(-8, 9, (5, 24))
+    B = rng.integers(-8, 9, (7, 24))          # stored as Bt: row j is column j of B
+    C, S = OT.gemm_bf16(_bf16_of_ints(A), _bf16_of_ints(B))
+    assert C.shape == (5, 7)
+    assert np.array_equal(C, (A @ B.T).astype(np.float64))
+    assert np.array_equal(S, (np.abs(A) @ np.abs(B).T).astype(np.float64))
+    eye = _bf16_of_ints(np.eye(24))
+    C2, _ = OT.gemm_bf16(_bf16_of_ints(A), eye)
+    assert np.array_equal(C2, A.astype(np.float64))
+
+
+def test_gemm_bf16_matches_fp32_chain_within_its_bound(oracle_tenants):
+    OT = oracle_tenants
+    # the FP32 oracle's fused chain over bfloat16-valued inputs differs from the
+    # exact sum by at most K u sum|ab| (u = 2^-24)
+    inp = gen.gen_gemm_bf16(3, 1, 33, 20, 64)
+    a = OT.bf16_to_f64(inp["A"]).astype(np.float32)
+    b = OT.bf16_to_f64(inp["Bt"]).astype(np.float32)
+    c32 = OT.gemm_f32(a, np.ascontiguousarray(b.T)).astype(np.float64)
+    c64, s = OT.gemm_bf16(inp["A"], inp["Bt"])
+    assert np.all(np.abs(c32 - c64) <= 64 * 2.0 ** -24 * s)
+    ii = np.array([0, 5, 32, 17]); jj = np.array([0, 19, 3, 11])
+    cs, ss = OT.gemm_bf16_sample(inp["A"], inp["Bt"], ii, jj)
+    assert np.allclose(cs, c64[ii, jj], rtol=0, atol=1e-12) and np.allclose(ss, s[ii, jj], rtol=0, atol=1e-12)

@@ -122,6 +122,21 @@ def gen_gemm_f32(cs: int, ti: int, M: int, N: int, K: int) -> dict:
     return dict(A=A, B=B, M=M, N=N, K=K)
 
 
+def bf16_bits(x: np.ndarray) -> np.ndarray:
+    """bfloat16 bit patterns of float32 values, round to nearest even (the
+    input distribution of the BF16 GEMM: N(0,1) values that bfloat16 holds)."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    return r.astype(np.uint16)
+
+
+def gen_gemm_bf16(cs: int, ti: int, M: int, N: int, K: int) -> dict:
+    """A [M][K] and Bt [N][K] (B column-major) as bfloat16 bits from N(0,1)."""
+    A = bf16_bits(normal_f32(stream_seed(cs, ti, "A"), M * K)).reshape(M, K)
+    Bt = bf16_bits(normal_f32(stream_seed(cs, ti, "B"), N * K)).reshape(N, K)
+    return dict(A=A, Bt=Bt, M=M, N=N, K=K)
+
+
 def spmv_xm_for_mean(mean: float = 16.0, alpha: float = 2.5, dmax: int = 8192) -> float:
     """Lower bound x_m of a Pareto(pdf ~ x^-alpha) truncated at dmax+1 such
     that E[floor(X)] = mean (bisection on the closed-form expectation)."""
@@ -222,5 +237,5 @@ def gen_tenant(name: str, cs: int, ti: int, **size) -> dict:
     fn = {"gather": gen_gather, "blackscholes": gen_blackscholes,
           "gemm_f32": gen_gemm_f32, "spmv_csr": gen_spmv_csr, "pchase": gen_pchase,
           "triad": gen_triad, "hist256": gen_hist256, "escape": gen_escape,
-          "bitonic": gen_bitonic, "matadd": gen_matadd}[name]
+          "bitonic": gen_bitonic, "matadd": gen_matadd, "gemm_bf16": gen_gemm_bf16}[name]
     return fn(cs, ti, **size)
