@@ -259,6 +259,38 @@ def _measured_peaks():
 
 
 PROFILES = os.path.join(ROOT, "paper_1303_5164_gb300", "profiles_gb300.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "cosched_kernel_mix64_dram.txt")
+KERNEL_SOURCES = ["kl_cosched.cu", "tenants.cuh", "kl_internal.h"]
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the co-scheduler kernel's sources (the counters below are
+    only valid for the kernel they were taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1303_5164_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _measured_traffic(workload: str):
+    """DRAM bytes per cosched_kernel launch from the committed ncu summary, or
+    None when it is missing, for another workload, or taken on other sources."""
+    if not os.path.exists(TRAFFIC):
+        return None
+    kv = {}
+    with open(TRAFFIC) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("workload") != workload or kv.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def _load_profiles(K, path=PROFILES):
@@ -534,7 +566,7 @@ def run_ours(args):
             "mix_roofline": {"t_roof_ms": t_roof * 1e3, "frac": (t_roof * 1e3) / kern_ms,
                              "algo_bytes": bytes_mix, "fp32_flops": flops_mix},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
-                         "frac": achieved / hbm_gbs, "traffic": None,
+                         "frac": achieved / hbm_gbs, "traffic": _measured_traffic(args.workload),
                          "kernel": "cosched_kernel", "kernel_ms": kern_ms,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback 6800 GB/s"},

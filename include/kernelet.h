@@ -223,7 +223,8 @@ typedef enum {
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their
                                slices first, so their stage barriers overlap
-                               other work instead of forming the end of the run */
+                               other work instead of forming the end of the run;
+                               default on, kl_config.chain_slots = 2 */
 
 typedef struct {
     int32_t device;                 /* CUDA ordinal (default 0)                     */

@@ -62,6 +62,14 @@ TYPE_OF_KERNEL = {f"native_kernel<{i}>": n for i, n in enumerate(
     ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256", "escape", "bitonic",
      "matadd", "gemm_bf16"])}
 
+# Types left out of the a0/b0 fit, with the reason (their errors are still
+# reported): the Markov model's warps are either ready or waiting on memory.
+FIT_EXCLUDE = {
+    "matadd": "one wave of 256 short blocks: never reaches the steady state the chain describes",
+    "gemm_bf16": "operands arrive by TMA (not counted as loads) and 7 of 8 warps wait at barriers while "
+                 "one thread issues tensor-core MMAs: neither state is in the model",
+}
+
 # working sets at or under half of L2 see the L2 latency, larger ones DRAM's
 L2_RESIDENT = {"gemm_f32", "bitonic", "pchase", "gather", "matadd", "gemm_bf16"}
 
@@ -196,20 +204,23 @@ def ingest(csv_path, latency_json, out_path, hbm_gbs=None, n_sm=None):
             err[name] = K.model_ipc(mp, [p], [W], 3)[0]
         return err
 
+    fit = [n for n in types if n not in FIT_EXCLUDE]
     best = None
     for a0 in (0.125, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0):
         for b0 in (0.0, 100.0, 200.0, 400.0, 800.0):
             pred = predict(a0, b0)
-            sse = sum((pred[n] - types[n]["ipc_measured"]) ** 2 for n in types)
+            sse = sum((pred[n] - types[n]["ipc_measured"]) ** 2 for n in fit)
             if best is None or sse < best[0]:
                 best = (sse, a0, b0, pred)
     _, a0, b0, pred = best
     for n in types:
         types[n]["ipc_predicted"] = pred[n]
-    mae = sum(abs(pred[n] - types[n]["ipc_measured"]) for n in types) / max(1, len(types))
+    mae = sum(abs(pred[n] - types[n]["ipc_measured"]) for n in fit) / max(1, len(fit))
     out = {"source": f"ncu counters on GB300 ({os.path.basename(csv_path)}), latency probe",
            "n_sm": nsm, "f_sm_hz": f, "dram_bytes_per_s": hbm, "a0": a0, "b0": b0,
-           "ipc_mae_per_sm": mae, "ipc_peak_per_sm": 4.0, "latency": lat, "types": types}
+           "ipc_mae_per_sm": mae, "ipc_mae_types": fit,
+           "fit_excluded": {n: FIT_EXCLUDE[n] for n in types if n in FIT_EXCLUDE},
+           "ipc_peak_per_sm": 4.0, "latency": lat, "types": types}
     with open(out_path, "w") as fh:
         json.dump(out, fh, indent=1, sort_keys=True)
     print(json.dumps({"a0": a0, "b0": b0, "ipc_mae_per_sm": mae,
