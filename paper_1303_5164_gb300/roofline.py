@@ -35,7 +35,16 @@ def algo_bytes(name: str, inp: dict) -> int:
         return 8 * inp["n"]
     if name == "matadd":
         return 12 * inp["n"] * inp["n"]
+    if name == "gemm_bf16":
+        return 2 * (inp["M"] * inp["K"] + inp["N"] * inp["K"]) + 4 * inp["M"] * inp["N"]
     raise ValueError(name)
+
+
+def tensor_flops(name: str, inp: dict) -> int:
+    """Operations on the tensor cores (the BF16 GEMM: 2 M N K)."""
+    if name == "gemm_bf16":
+        return 2 * inp["M"] * inp["N"] * inp["K"]
+    return 0
 
 
 def fp32_flops(name: str, inp: dict, escape_iters: int | None = None) -> int:
