@@ -40,6 +40,25 @@ WORKLOAD = ("8-tenant mix, 64 kernels (8 each of FP32 GEMM 1024^3, CSR SpMV 1Mi 
             "Zipf(1.1), escape-time 2048^2 max 256, bitonic 2^22), seeded order")
 
 
+# ---------------------------------------------------------------------- ranks
+
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The slowest rank's value (the step time every rank waits for)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(kernels_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: kernels all ranks processed per second of the
+    slowest rank's step (replicas: every rank runs its own batch)."""
+    return world * kernels_per_rank / (ms_per_step / 1e3)
+
+
 # ---------------------------------------------------------------------- inputs
 
 def _gen_one(job):
@@ -409,6 +428,8 @@ def run_ours(args):
     cfg = K.config_default()
     cfg.device = local
     cfg.max_tenants = 4096
+    if args.flags is not None:
+        cfg.flags = args.flags
     rt = K.Runtime(cfg, stream=stream.cuda_stream)
     hbm_gbs, peak_src = _measured_peaks()
     mp_ = rt.model_params()
@@ -459,12 +480,7 @@ def run_ours(args):
                 collect(hs)
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world, "cuda")
 
     for _ in range(args.warmup):
         step_cosched()
@@ -497,7 +513,7 @@ def run_ours(args):
     ms_se = timed(lambda: step_base(K.KL_BASE_SERIAL, 1), args.steps)
 
     n = len(tens)
-    value = world * n / (ms_co / 1e3)
+    value = job_value(n, world, ms_co)
 
     # roofline of the dominant (only) kernel: the persistent co-scheduler
     esc_iters = {}
@@ -618,6 +634,8 @@ def run_serve(args):
     cfg = K.config_default()
     cfg.device = local
     cfg.max_tenants = 4 * n_sm
+    if args.flags is not None:
+        cfg.flags = args.flags
     cfg.mem_cap_bytes = 150 * 10**9
     stream = torch.cuda.Stream()  # the serving kernel holds its stream for the whole run
     rt = K.Runtime(cfg, stream=stream.cuda_stream)
@@ -748,6 +766,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-rates", default="100,300,1000,3000,10000,20000")
     ap.add_argument("--serve-replicas", type=int, default=24)
+    ap.add_argument("--flags", type=int, default=None, help="kl_config.flags (default: the library's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -219,6 +219,13 @@ typedef enum {
                                run KL_T_GEMM_BF16 (tensor cores); without it a
                                serving run refuses that type (KL_EINVAL). Batch
                                runs pick the build from the kernels they hold. */
+#define KL_CFG_WIDE_FILL 16u /* backfill considers 8 pending kernels per phase
+                               (both chain-lane kernels, then the lowest pending
+                               ones) instead of 4; default on */
+#define KL_CFG_LAZY_ARRIVAL 32u /* serving: an arrival re-plans only when no pair is
+                               running (idle or solo phase); otherwise the new
+                               kernel waits in R for the next re-plan, which
+                               comes when a kernel of the pair runs out */
 #define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their
@@ -239,6 +246,13 @@ typedef struct {
     uint32_t flags;                 /* KL_CFG_* bits                                */
     uint32_t chain_slots;           /* KL_CFG_CHAIN_LANE: slots per SM (the last ones)
                                        that serve multi-stage kernels first; 0 = 1 */
+    uint64_t age_limit_ns;          /* serving: a kernel pending longer than this
+                                       (device clock, since the device took it in) is
+                                       put into the next co-schedule with its best
+                                       partner, so poorly pairing kernels are not
+                                       starved by new arrivals; 0 = 5 ms; ~0 = off.
+                                       Batch runs never age (every kernel is present
+                                       from the start). */
 } kl_config;
 
 /* Model inputs for one tenant type (Table 1 parameters, measured by profiling
@@ -306,6 +320,10 @@ typedef struct {
                                    scheduled run) or of the fork/join (baseline) */
     uint64_t run_ns;            /* CUDA-event time from the run's first copy to
                                    its last (descriptors in, results out)        */
+    uint64_t slot_wait_ns;      /* co-scheduled: summed over CTAs, time with no
+                                   slice to pull (idle slots)                    */
+    uint64_t stage_wait_ns;     /* ... time at a stage barrier inside a slice     */
+    uint64_t plan_ns;           /* ... time re-planning (FindCoSchedule)          */
 } kl_run_stats;
 
 typedef enum {

@@ -87,6 +87,7 @@ struct CtaCtl {
   int32_t wait_failed;
   uint32_t from, to;   // dispatcher: kernels to copy in
   uint32_t mine;       // dispatcher: this CTA claimed the re-plan
+  unsigned long long acc_wait, acc_stage, acc_plan;  // this CTA's time accounting (thread 0)
 };
 
 __device__ __forceinline__ void set_error(RunDev* R, int32_t code, uint32_t info) {
@@ -135,7 +136,7 @@ struct ScanPart {
   int32_t first;
   unsigned long long pmask;
   uint32_t nlow, nms;
-  int32_t lowp[6];
+  int32_t lowp[10];
   int32_t lowms[4];
   int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
 };
@@ -153,7 +154,7 @@ static_assert(kPlanScratch <= tn::kMinCtaSmem, "re-plan scratch fits the smalles
 // pairs (all pairs when every one is pruned), ties to the smallest (i, j). One
 // pending kernel runs alone on every slot; none ends a batch run, or idles a
 // serving run until the next arrival.
-__device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, int32_t trigger, char* smem) {
+__device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, int32_t trigger, char* smem) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ScanPart* parts = reinterpret_cast<ScanPart*>(smem);
   uint32_t* bounds = reinterpret_cast<uint32_t*>(parts + kWarps);
@@ -169,7 +170,7 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
     for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
     uint32_t npend = 0, nlow = 0, nms = 0;
     unsigned long long pmask = 0ull;
-    int32_t lowp[6], lowms[4];
+    int32_t lowp[10], lowms[4];
     int32_t first_pending = -1;
     const uint32_t nchunk = hi > lo ? (hi - lo + 31u) / 32u : 0u;
     const uint32_t cpw = (nchunk + kWarps - 1) / kWarps;
@@ -190,7 +191,7 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
       npend += __popc(pb);
       if (pb && first_pending < 0) first_pending = (int32_t)(base + __ffs(pb) - 1);
       if (base < 64) pmask |= (unsigned long long)pb << base;
-      for (uint32_t m = pb; m && nlow < 6; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
+      for (uint32_t m = pb; m && nlow < 10; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
       const uint32_t msb = __ballot_sync(0xffffffffu, pend && multi);
       for (uint32_t m = msb; m && nms < 4; m &= m - 1) lowms[nms++] = (int32_t)(base + __ffs(m) - 1);
 #pragma unroll
@@ -226,14 +227,14 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
   for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
   uint32_t npend = 0, nlow = 0, nms = 0;
   unsigned long long pmask = 0ull;
-  int32_t lowp[6], lowms[4];
+  int32_t lowp[10], lowms[4];
   int32_t first_pending = -1;
   for (int w = 0; w < kWarps; ++w) {
     const ScanPart& q = parts[w];
     npend += q.npend;
     pmask |= q.pmask;
     if (first_pending < 0) first_pending = q.first;
-    for (uint32_t f = 0; f < q.nlow && nlow < 6; ++f) lowp[nlow++] = q.lowp[f];
+    for (uint32_t f = 0; f < q.nlow && nlow < 10; ++f) lowp[nlow++] = q.lowp[f];
     for (uint32_t f = 0; f < q.nms && nms < 4; ++f) lowms[nms++] = q.lowms[f];
     for (int t = 0; t < KL_T_COUNT; ++t) {
       const int32_t c[2] = {q.low1[t], q.low2[t]};
@@ -263,7 +264,38 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
     for (int t = 0; t < KL_T_COUNT; ++t)
       if (low1[t] >= 0) ph.A = low1[t];
   } else if (npend >= 2) {
-    for (int pass = 0; pass < 2; ++pass) {
+    // serving: the oldest pending kernel (lowest sequence number) has waited
+    // past the age limit: it goes first, with its best partner by CP
+    int32_t aged = -1;
+    if (R->serve && first_pending >= 0 && R->age_limit_ns != ~0ull) {
+      const unsigned long long ta = __ldcg(&tenant(T, R, (uint32_t)first_pending).t_arrive);
+      if (ta != 0ull && gtimer() - ta > R->age_limit_ns) aged = first_pending;
+    }
+    if (aged >= 0) {
+      const uint32_t tya = tenant(T, R, (uint32_t)aged).type;
+      double best = 0.0;
+      int32_t bj = -1;
+      for (int pass = 0; pass < 2 && bj < 0; ++pass)
+        for (int tb = 0; tb < KL_T_COUNT; ++tb) {
+          const int32_t j = low1[tb] != aged ? low1[tb] : low2[tb];
+          if (j < 0) continue;
+          const uint32_t tyj = tenant(T, R, (uint32_t)j).type;
+          if (pass == 0 && !R->allowed[tya][tyj]) continue;
+          const double c = R->cp[tya][tyj];
+          if (bj < 0 || c > best + 1e-12 || (fabs(c - best) <= 1e-12 && j < bj)) {
+            best = c;
+            bj = j;
+          }
+        }
+      if (bj >= 0) {
+        ph.A = aged;
+        ph.B = bj;
+        ph.cp = best;
+        ph.slots_a = R->slots_a[tya][tenant(T, R, (uint32_t)bj).type];
+        ph.slots_b = R->slots - ph.slots_a;
+      }
+    }
+    for (int pass = 0; pass < 2 && aged < 0; ++pass) {
       double best = 0.0;
       int32_t bi = -1, bj = -1;
       for (int ta = 0; ta < KL_T_COUNT; ++ta) {
@@ -306,7 +338,8 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
   // kernel (a long chain of dependent grids: started early, its stage
   // barriers overlap other work instead of forming the tail of the run), then
   // the lowest pending sequence numbers
-  for (int f = 0; f < 4; ++f) ph.fill[f] = -1;
+  for (int f = 0; f < kFill; ++f) ph.fill[f] = -1;
+  const uint32_t nfill = (R->flags & KL_CFG_WIDE_FILL) ? (uint32_t)kFill : 4u;
   uint32_t c = 0;
   if (ph.A >= 0 && (R->flags & KL_CFG_FILL_TYPES)) {
     const uint32_t ta = tenant(T, R, ph.A).type;
@@ -325,9 +358,13 @@ __device__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t seq_old, i
     for (uint32_t f = 0; f < nms && nc < 2; ++f)
       if (lowms[f] != ph.A && lowms[f] != ph.B) ph.chain[nc++] = lowms[f];
   }
-  if (ph.chain[0] >= 0 && c < 4 && (c == 0 || ph.chain[0] != ph.fill[0]) && (c < 2 || ph.chain[0] != ph.fill[1]))
-    ph.fill[c++] = ph.chain[0];
-  for (uint32_t f = 0; f < nlow && c < 4; ++f) {
+  for (int k = 0; k < 2 && c < nfill; ++k) {
+    bool dup = ph.chain[k] < 0;
+    for (uint32_t q = 0; q < c; ++q) dup |= ph.chain[k] == ph.fill[q];
+    if (!dup) ph.fill[c++] = ph.chain[k];
+    if (!(R->flags & KL_CFG_WIDE_FILL)) break;  // the narrow list takes the lowest chain only
+  }
+  for (uint32_t f = 0; f < nlow && c < nfill; ++f) {
     bool dup = lowp[f] == ph.A || lowp[f] == ph.B;
     for (uint32_t q = 0; q < c; ++q) dup |= lowp[f] == ph.fill[q];
     if (!dup) ph.fill[c++] = lowp[f];
@@ -431,6 +468,11 @@ __device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl, ch
           unsigned long long* dst = reinterpret_cast<unsigned long long*>(&T[s & R->ring_mask]);
           dst[tid] = ld_volatile64(src + tid);
         }
+        __syncwarp();
+        if (tid == 0) {
+          const unsigned long long now = gtimer();
+          for (uint32_t s = ctl.from; s < ctl.to; ++s) T[s & R->ring_mask].t_arrive = now;
+        }
         __threadfence();
       }
       __syncthreads();
@@ -440,7 +482,11 @@ __device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl, ch
         st_release(&R->intake, ctl.to);
         const uint32_t seq = ld_acquire(&R->phase_seq);
         ctl.seq = seq;
-        ctl.mine = ld_relaxed(&R->phase_claim) == seq && atomicCAS(&R->phase_claim, seq, seq + 1) == seq;
+        // KL_CFG_LAZY_ARRIVAL: a running pair keeps the GPU; arrivals join R
+        // and are planned when a kernel of the pair runs out
+        const bool pair_running = __ldcg(&phase(P, R, seq)->B) >= 0;
+        ctl.mine = !((R->flags & KL_CFG_LAZY_ARRIVAL) && pair_running) && ld_relaxed(&R->phase_claim) == seq &&
+                   atomicCAS(&R->phase_claim, seq, seq + 1) == seq;
       }
       __syncthreads();
       if (ctl.mine) replan(T, R, P, ctl.seq, -1, smem);
@@ -480,6 +526,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
   const unsigned long long limit = R->wait_limit_ns;
   unsigned long long wait_since = 0;
   uint32_t backoff = 32;
+  if (tid == 0) ctl.acc_wait = ctl.acc_stage = ctl.acc_plan = 0ull;
 
   for (;;) {
     if (tid == 0) {
@@ -502,7 +549,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
           int32_t trig = -1;
           // serving: kernels arrived after this plan was made; re-plan now
           if (R->serve && ld_relaxed(&R->intake) > __ldcg(&pp->intake_seen) &&
-              ld_relaxed(&R->phase_claim) == seq && atomicCAS(&R->phase_claim, seq, seq + 1) == seq) {
+              !((R->flags & KL_CFG_LAZY_ARRIVAL) && __ldcg(&pp->B) >= 0) && ld_relaxed(&R->phase_claim) == seq &&
+              atomicCAS(&R->phase_claim, seq, seq + 1) == seq) {
             ctl.action = kActReplan;
             ctl.seq = seq;
             ctl.trigger = -1;
@@ -572,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
           // spread rule, re-plan in flight), so take a slice of another
           // pending kernel instead of idling
           if (ctl.action == kActWait && (R->flags & KL_CFG_BACKFILL) && ph.A >= 0) {
-            for (int f = 0; f < 4; ++f) {
+            for (int f = 0; f < kFill; ++f) {
               const int32_t c = __ldcg(&pp->fill[f]);
               if (c < 0) break;
               uint32_t g0 = 0, g1 = 0;
@@ -600,6 +648,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
           backoff = min(backoff * 2, 256u);
         }
       } else {
+        if (wait_since != 0) ctl.acc_wait += gtimer() - wait_since;
         wait_since = 0;
         backoff = 32;
       }
@@ -608,7 +657,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     const uint32_t action = ctl.action;
     if (action == kActExit) break;
     if (action == kActReplan) {
+      const unsigned long long t0 = tid == 0 ? gtimer() : 0ull;
       replan(T, R, P, ctl.seq, ctl.trigger, smem);
+      if (tid == 0) ctl.acc_plan += gtimer() - t0;
     } else if (action == kActRun) {
       TenantDev& d = tenant(T, R, (uint32_t)ctl.tenant);
       const uint32_t type = d.type;
@@ -631,6 +682,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
               __nanosleep(bo);
               bo = min(bo * 2, 256u);
             }
+            ctl.acc_stage += gtimer() - since;
           }
           __syncthreads();
           if (ctl.wait_failed) break;
@@ -654,7 +706,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
     __syncthreads();
   }
   if constexpr (TC) tn::release_tmem(tcx);
-  if (tid == 0) atomicAdd(&R->ctas_done, 1u);
+  if (tid == 0) {
+    atomicAdd(&R->wait_ns, ctl.acc_wait);
+    atomicAdd(&R->stage_wait_ns, ctl.acc_stage);
+    atomicAdd(&R->plan_ns, ctl.acc_plan);
+    atomicAdd(&R->ctas_done, 1u);
+  }
 }
 
 // ------------------------------------------------------------------ host side

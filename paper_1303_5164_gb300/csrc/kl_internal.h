@@ -9,6 +9,7 @@ namespace kl {
 constexpr int kThreads = KL_BLOCK_THREADS;
 constexpr int kMaxSM = 256;
 constexpr int kNoTenant = -1;
+constexpr int kFill = 8;      // backfill candidates per phase (4 unless KL_CFG_WIDE_FILL)
 
 // One submitted kernel in device memory (128-byte aligned, 256 bytes).
 // Static fields are written by the host before the launch; dynamic fields are
@@ -20,7 +21,8 @@ struct alignas(128) TenantDev {
   uint32_t total;         // thread blocks summed over stages
   uint32_t nstages;
   uint32_t index;         // submit index within the run
-  uint32_t pad0[3];
+  uint32_t pad0;
+  unsigned long long t_arrive;  // serving: globaltimer when the device took the kernel in
   alignas(16) unsigned char args[KL_MAX_ARGS_BYTES];
   // ---- dynamic (own 128-byte line, away from the arguments)
   alignas(128) uint32_t next;     // next block to hand out (cumulative over stages)
@@ -42,7 +44,7 @@ struct PhaseDev {
   int32_t trigger;
   uint32_t n_pending;          // kernels with blocks left when the phase was chosen
   unsigned long long pending;  // bit i: kernel i (i < 64) was pending
-  int32_t fill[4];             // other pending kernels (lowest indices) for backfill
+  int32_t fill[kFill];         // other pending kernels for backfill (-1 ends the list)
   uint32_t done_a, done_b;     // blocks finished by this phase's A, B when it was published
   uint32_t prev_done_a;        // ... and by the previous phase's A, B at the same moment
   uint32_t prev_done_b;
@@ -50,7 +52,7 @@ struct PhaseDev {
   uint32_t pad2;
   int32_t chain[2];            // lowest pending multi-stage kernels outside A, B (chain lane)
 };
-static_assert(sizeof(PhaseDev) == 96, "PhaseDev layout");
+static_assert(sizeof(PhaseDev) == 112, "PhaseDev layout");
 
 // Serving mode: per-kernel completion record in mapped host memory, written
 // by the device before the kernel's entry in the completion queue.
@@ -79,6 +81,7 @@ struct alignas(128) RunDev {
   uint32_t serve;              // 1: serving mode (tenant ring, dispatcher CTA 0)
   uint32_t chain_slots;        // chain lane: the last chain_slots slots of every SM
   uint32_t pad_s;
+  unsigned long long age_limit_ns;    // serving: pending longer than this -> paired first
   unsigned long long wait_limit_ns;
   uint32_t ring_mask;          // tenant slots - 1 (power of two); tenant seq -> slot
   uint32_t phase_mask;         // phase slots - 1 (power of two)
@@ -102,6 +105,9 @@ struct alignas(128) RunDev {
   uint32_t intake;                   // serving: kernels copied into the device ring
   uint32_t scan_lo;                  // lowest sequence number that may still be pending
   uint32_t cq_pos;                   // serving: completion queue entries written
+  unsigned long long wait_ns;        // summed over CTAs: time with nothing to pull
+  unsigned long long stage_wait_ns;  // summed over CTAs: time at stage barriers inside a slice
+  unsigned long long plan_ns;        // summed over CTAs: time re-planning
   alignas(128) uint32_t sm_ticket[kMaxSM];
 };
 

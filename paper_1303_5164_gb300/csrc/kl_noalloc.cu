@@ -132,7 +132,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
     }
   img.ph0.A = -2;
   img.ph0.B = -1;
-  for (int f = 0; f < 4; ++f) img.ph0.fill[f] = -1;
+  for (int f = 0; f < kFill; ++f) img.ph0.fill[f] = -1;
   img.ph0.chain[0] = img.ph0.chain[1] = -1;
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

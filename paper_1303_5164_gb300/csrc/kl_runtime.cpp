@@ -405,6 +405,9 @@ int retire_serve(kl_runtime* rt) {
     rt->last.n_phases = (uint32_t)std::min<uint64_t>(np, 0xffffffffu);
     rt->last.t_launch_ns = R.t_launch;
     rt->last.t_end_ns = R.t_end;
+    rt->last.slot_wait_ns = R.wait_ns;
+    rt->last.stage_wait_ns = R.stage_wait_ns;
+    rt->last.plan_ns = R.plan_ns;
   } else {
     rt->last = kl_run_stats{};
     rt->last_phases.clear();
@@ -502,6 +505,9 @@ int retire(kl_runtime* rt) {
     rt->last.grid_ctas = rt->slots * rt->n_sm;
     rt->last.t_launch_ns = R.t_launch;
     rt->last.t_end_ns = R.t_end;
+    rt->last.slot_wait_ns = R.wait_ns;
+    rt->last.stage_wait_ns = R.stage_wait_ns;
+    rt->last.plan_ns = R.plan_ns;
     float ms = 0.f;
     rt->last.kernel_ns =
         cudaEventElapsedTime(&ms, rt->ev_k0, rt->ev_k1) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
@@ -668,7 +674,7 @@ extern "C" int kl_config_default(kl_config* c) {
   c->mem_cap_bytes = 0;
   c->alpha_p = -1.0;
   c->alpha_m = -1.0;
-  c->flags = KL_CFG_BACKFILL | KL_CFG_FILL_TYPES | KL_CFG_CHAIN_LANE;
+  c->flags = KL_CFG_BACKFILL | KL_CFG_FILL_TYPES | KL_CFG_CHAIN_LANE | KL_CFG_WIDE_FILL;
   c->chain_slots = 2;
   return KL_OK;
 }
@@ -912,7 +918,7 @@ static int launch_locked(kl_runtime* rt) {
   PhaseDev first{};
   first.A = -2;
   first.B = -1;
-  for (int f = 0; f < 4; ++f) first.fill[f] = -1;
+  for (int f = 0; f < kFill; ++f) first.fill[f] = -1;
   first.chain[0] = first.chain[1] = -1;
   rt->h_phases[0] = first;
   cudaStream_t s = rt->stream;
@@ -1057,6 +1063,7 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     R.flags = rt->cfg.flags;
     R.serve = 1;
     R.chain_slots = std::max(1u, std::min(rt->cfg.chain_slots, rt->slots - 1));
+    R.age_limit_ns = rt->cfg.age_limit_ns ? rt->cfg.age_limit_ns : 5000000ull;
     R.ring_mask = rt->s_ring - 1u;
     R.phase_mask = rt->s_phase_slots - 1u;
     R.idle_limit_ns = idle_limit_ns ? idle_limit_ns : 60000000000ull;
@@ -1070,15 +1077,19 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     PhaseDev first{};
     first.A = kPhasePlan;
     first.B = -1;
-    for (int f = 0; f < 4; ++f) first.fill[f] = -1;
+    for (int f = 0; f < kFill; ++f) first.fill[f] = -1;
     first.chain[0] = first.chain[1] = -1;
     rt->sh_phases[0] = first;
     rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->sd_phases, rt->sh_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
     if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
-    if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, tn::kMaxTenantSmem,
-                              (rt->cfg.flags & KL_CFG_SERVE_TC) != 0, s) != 0)
+    // dynamic shared memory of the largest type a serving run can receive
+    const bool tc = (rt->cfg.flags & KL_CFG_SERVE_TC) != 0;
+    uint32_t smem = tn::kMinCtaSmem;
+    for (uint32_t t = 0; t < KL_T_COUNT; ++t)
+      if (t != KL_T_GEMM_BF16 || tc) smem = std::max(smem, tn::smem_bytes(t));
+    if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, smem, tc, s) != 0)
       rc = KL_ECUDA;
     if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));

@@ -31,6 +31,8 @@ KL_CFG_BACKFILL = 1
 KL_CFG_FILL_TYPES = 2
 KL_CFG_CHAIN_LANE = 4
 KL_CFG_SERVE_TC = 8
+KL_CFG_WIDE_FILL = 16
+KL_CFG_LAZY_ARRIVAL = 32
 
 P = C.c_void_p
 U32, U64, I32, F32, F64 = C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
@@ -102,7 +104,7 @@ class kl_config(C.Structure):
     _fields_ = [("device", I32), ("slots_per_sm", U32), ("max_tenants", U32), ("model_states", U32),
                 ("ratio_policy", U32), ("fixed_slots_a", U32), ("device_wait_limit_ns", U64),
                 ("mem_cap_bytes", U64), ("alpha_p", F64), ("alpha_m", F64), ("flags", U32),
-                ("chain_slots", U32)]
+                ("chain_slots", U32), ("age_limit_ns", U64)]
 
 
 class kl_profile(C.Structure):
@@ -131,7 +133,8 @@ class kl_tenant_stats(C.Structure):
 class kl_run_stats(C.Structure):
     _fields_ = [("n_tenants", U32), ("n_phases", U32), ("error", I32), ("slots_per_sm", U32),
                 ("grid_ctas", U32), ("pad", U32), ("t_launch_ns", U64), ("t_end_ns", U64),
-                ("kernel_ns", U64), ("run_ns", U64)]
+                ("kernel_ns", U64), ("run_ns", U64), ("slot_wait_ns", U64), ("stage_wait_ns", U64),
+                ("plan_ns", U64)]
 
 
 class KLError(RuntimeError):

@@ -2,11 +2,13 @@
 single-kernel and concurrent-kernel IPC prediction, CP prediction).
 
 Every kernel type runs alone in the co-scheduler, then every pair of types
-runs co-scheduled at the model's balanced slot split (Eq. executiontime). The
-measured IPC of a kernel in a phase is its blocks finished during the phase
-(from the phase log) times its instructions per block (measured with ncu)
-over the phase's cycles on all SMs. The model's numbers come from the
-runtime's own model with the measured per-type profiles.
+runs co-scheduled at the model's balanced slot split (Eq. executiontime), 8
+copies of each kernel per run with backfill and the chain lane off, so that
+the phases are pure pairs in steady state. The measured IPC of a type is its
+blocks finished during the phases that run exactly that pair (from the phase
+log) times its instructions per block (measured with ncu) over those phases'
+cycles on all SMs. The model's numbers come from the runtime's own model with
+the measured per-type profiles.
 
 The two-tenant case (Black-Scholes 65,536 options + int32 gather 2^20, each
 in 4 slices) is repeated 1000 times inside one persistent launch at fixed slot
@@ -29,6 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 TYPES = ["gemm_f32", "spmv_csr", "blackscholes", "pchase", "triad", "hist256", "escape", "bitonic"]
+COPIES = 8
 
 
 def _profiles(K):
@@ -81,41 +84,82 @@ def run(out_path, reps=3):
     tens = {t: T.make(t, gen.gen_tenant(t, 9, i, **T.SIZES_MIX[t])) for i, t in enumerate(TYPES)}
     res = {"slots_per_sm": S, "f_sm_hz": mp.f_sm_hz, "n_sm": mp.n_sm, "solo": {}, "pairs": {}}
 
-    def go(names, policy=K.KL_RATIO_BALANCED, fixed=2, slices=None):
+    # 8 copies of each kernel per run (inputs shared, outputs replicated) and
+    # no backfill or chain lane: every phase is a pure pair (or a solo phase)
+    # and the pair persists across phases until one type runs out
+    reps_of = {nm: [tens[nm]] + [tens[nm].replica() for _ in range(COPIES - 1)] for nm in TYPES}
+
+    def go(names):
         c2 = K.config_default()
         c2.slots_per_sm = S
-        c2.ratio_policy = policy
-        c2.fixed_slots_a = fixed
+        c2.flags = 0
+        c2.max_tenants = 4096
+        # prune only pairs with identical PUR and MUR (two copies of one type):
+        # while both types are pending the pair (a, b) runs; once one type is
+        # left its copies pair with each other (every pair pruned -> unpruned set)
+        c2.alpha_p = c2.alpha_m = 1e-9
         r2 = K.Runtime(c2)
         r2.set_model_params(mp)
         r2.set_profiles(profs)
         best = None
         for _ in range(reps):
-            for j, nm in enumerate(names):
-                r2.submit(tens[nm].type, tens[nm].args, slice_blocks=(slices[j] if slices else 0))
+            order = [nm for k in range(COPIES) for nm in names]
+            for k, nm in enumerate(order):
+                t = reps_of[nm][k // len(names)]
+                r2.submit(t.type, t.args)
             r2.launch()
             assert r2.drain() == 0
-            ph = r2.phases()
             ker = r2.run_stats().kernel_ns / 1e3
             if best is None or ker < best[1]:
-                best = (ph, ker)
+                best = (r2.phases(), ker, order)
         r2.close()
         return best
 
+    def steady_ipc(ph, order, names):
+        """Per-type IPC per SM summed over the phases that run exactly the
+        types in `names` (both of a pair, or the one type alone): blocks each
+        role finished during the phase x instructions per block over the
+        phase's cycles on all SMs."""
+        want = sorted(names)
+        blocks = {nm: 0 for nm in names}
+        cyc = 0.0
+        splits = []
+        for k in range(1, len(ph) - 1):
+            p, q = ph[k], ph[k + 1]
+            if p.A < 0:
+                continue
+            types = sorted([order[p.A]] + ([order[p.B]] if p.B >= 0 else []))
+            if (len(want) == 1 and set(types) != set(want)) or (len(want) == 2 and types != want):
+                continue
+            c = (q.t_ns - p.t_ns) * 1e-9 * mp.f_sm_hz
+            if c <= 0:
+                continue
+            cyc += c
+            blocks[order[p.A]] += q.prev_done_a - p.done_a
+            if p.B >= 0:
+                blocks[order[p.B]] += q.prev_done_b - p.done_b
+            splits.append(p.slots_a if order[p.A] == names[0] else S - p.slots_a)
+        if cyc <= 0:
+            return [None] * len(names), 0.0, None
+        ipc = [blocks[nm] * profs[tens[nm].type].I_block / (cyc * mp.n_sm) for nm in names]
+        sa = max(set(splits), key=splits.count) if splits and len(names) == 2 else None
+        return ipc, cyc / mp.f_sm_hz * 1e6, sa
+
     # solo IPC of each type at the co-scheduler's full occupancy
     for nm in TYPES:
-        ph, ker = go([nm])
-        (ipc, _), dur = _phase_ipc(ph, 1, [tens[nm]], profs, mp)
+        ph, ker, order = go([nm])
+        (ipc,), dur, _ = steady_ipc(ph, order, [nm])
         w = max(1, int(round(S * 8 / 4)))
         pred = K.model_ipc(mp, [profs[tens[nm].type]], [w], 3)[0]
-        res["solo"][nm] = {"ipc_measured": ipc, "ipc_predicted": pred, "phase_us": dur, "kernel_us": ker}
+        res["solo"][nm] = {"ipc_measured": ipc, "ipc_predicted": pred, "phases_us": dur, "kernel_us": ker}
         print("solo", nm, res["solo"][nm], flush=True)
 
     # all pairs at the model's balanced split
     for a, b in itertools.combinations(TYPES, 2):
-        ph, ker = go([a, b])
-        (ca, cb), dur = _phase_ipc(ph, 1, [tens[a], tens[b]], profs, mp)
-        sa = ph[1].slots_a
+        ph, ker, order = go([a, b])
+        (ca, cb), dur, sa = steady_ipc(ph, order, [a, b])
+        if sa is None:
+            sa = ph[1].slots_a if ph[1].A >= 0 and order[ph[1].A] == a else S - ph[1].slots_a
         pr = K.model_pair(mp, profs[tens[a].type], profs[tens[b].type], S, 3)
         pa, pb = pr["cipc_a"][sa - 1], pr["cipc_b"][sa - 1]
         ia, ib = res["solo"][a]["ipc_measured"], res["solo"][b]["ipc_measured"]
@@ -123,8 +167,10 @@ def run(out_path, reps=3):
         res["pairs"][f"{a}+{b}"] = {
             "slots_a": sa, "slots_b": S - sa, "cipc_measured": [ca, cb], "cipc_predicted": [pa, pb],
             "ipc_sum_measured": (ca or 0) + (cb or 0), "ipc_sum_predicted": pa + pb,
-            "cp_predicted": pr["cp"][sa - 1], "cp_measured": cp_meas, "phase_us": dur, "kernel_us": ker}
+            "cp_predicted": pr["cp"][sa - 1], "cp_measured": cp_meas, "pair_phases_us": dur, "kernel_us": ker}
         print("pair", a, b, json.dumps(res["pairs"][f"{a}+{b}"]), flush=True)
+    del reps_of
+    torch.cuda.empty_cache()
 
     # the two-tenant case (configs: Black-Scholes 65,536 + gather 2^20, 4 slices
     # each) repeated 1000 times inside ONE persistent launch, at slot ratios
