@@ -67,6 +67,49 @@ def test_errors_without_gpu(K):
     assert sh.nstages == 2 and sh.grid[0] == 1 and sh.total_blocks == 1 + 2048
 
 
+def test_serving_and_tensor_map_argument_checks_without_gpu(K):
+    L = K.lib()
+    n = K.U32()
+    buf = (K.U64 * 4)()
+    assert L.kl_serve_start(None, K.KL_SERVE_COSCHED, 0, 0) == K.KL_EINVAL
+    assert L.kl_serve_stop(None, 0) == K.KL_EINVAL
+    assert L.kl_reap(None, buf, 4, C.byref(n)) == K.KL_EINVAL
+    assert L.kl_run_noalloc(None, 0, None, None, None, 0, None) == K.KL_EINVAL
+    maps = (C.c_ubyte * 256)()
+    assert L.kl_gemm_bf16_tensor_maps(None, maps) == K.KL_EINVAL
+    bad = K.kl_args_gemm_bf16(16, 32, 48, 64, 128, 64, 100, 0)   # K not a multiple of 8
+    assert L.kl_gemm_bf16_tensor_maps(C.byref(bad), maps) == K.KL_EINVAL
+    sh = K.kl_tenant_shape()
+    assert L.kl_tenant_shape_of(K.KL_T_GEMM_BF16, C.byref(bad), C.sizeof(bad), C.byref(sh)) == K.KL_EINVAL
+    unaligned_maps = K.kl_args_gemm_bf16(16, 32, 48, 96, 128, 64, 128, 0)  # tensor maps not 64-byte aligned
+    assert L.kl_tenant_shape_of(K.KL_T_GEMM_BF16, C.byref(unaligned_maps), C.sizeof(unaligned_maps),
+                                C.byref(sh)) == K.KL_EINVAL
+    ok = K.kl_args_gemm_bf16(16, 32, 48, 64, 200, 132, 136, 0)
+    sh = K.tenant_shape(K.KL_T_GEMM_BF16, ok)
+    # 128 x 64 tiles: 2 x 3 with ragged edges, one stage, the largest shared memory of any type
+    assert tuple(sh.grid) == (6, 1, 1) and sh.nstages == 1 and sh.smem_bytes >= 48 * 1024
+    cfg = K.config_default()
+    assert cfg.flags & K.KL_CFG_BACKFILL and cfg.flags & K.KL_CFG_CHAIN_LANE and cfg.flags & K.KL_CFG_WIDE_FILL
+    assert cfg.chain_slots == 2 and cfg.age_limit_ns == 0
+
+
+def test_ctypes_structs_match_the_header(K, tmp_path):
+    # sizes of the ABI structs as gcc lays them out from include/kernelet.h,
+    # against the binding's ctypes declarations
+    names = ["kl_config", "kl_kernel_desc", "kl_tenant_shape", "kl_profile", "kl_model_params", "kl_phase",
+             "kl_tenant_stats", "kl_run_stats"] + [t.__name__ for t in K.ARGS_TYPES]
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "kernelet.h"\nint main(void) {\n' +
+                   "".join(f'  printf("%s %zu\\n", "{n}", sizeof({n}));\n' for n in names) + "  return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for n in names:
+        assert int(got[n]) == C.sizeof(getattr(K, n)), n
+    assert all(C.sizeof(t) <= K.KL_MAX_ARGS_BYTES for t in K.ARGS_TYPES)
+
+
 GPU = mk.GPUParams(n_sm=152, n_sched=4, f_sm_hz=1.9e9, dram_bytes_per_s=6753e9)
 
 
