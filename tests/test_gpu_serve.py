@@ -214,3 +214,31 @@ def test_serve_plain_launch_comparator(K, T, mode, nstreams):
         assert rt.stats(h).state == K.KL_DONE
         X.check(nm, x, t.fetch(), X.expected(nm, x))
     rt.close()
+
+
+def test_serve_tensor_core_build(K, T):
+    # serving with KL_CFG_SERVE_TC runs the BF16 GEMM among the arrivals;
+    # without it the type is refused
+    import torch
+    g_in = gen.gen_gemm_bf16(13, 0, 512, 256, 1024)
+    b_in = gen.gen_blackscholes(13, 1, 200000)
+    g, b = T.make("gemm_bf16", g_in), T.make("blackscholes", b_in)
+    torch.cuda.synchronize()
+    rt = _runtime(K)
+    rt.serve_start()
+    with pytest.raises(K.KLError) as e:
+        rt.submit(g.type, g.args)
+    assert e.value.code == K.KL_EINVAL
+    assert rt.serve_stop() == 0
+    rt.close()
+    c = K.config_default()
+    c.flags |= K.KL_CFG_SERVE_TC
+    rt = K.Runtime(c)
+    rt.serve_start()
+    hs = [rt.submit(g.type, g.args), rt.submit(b.type, b.args)]
+    for h in hs:
+        assert rt.wait(h, 20_000_000_000) == 0
+    assert rt.serve_stop() == 0
+    X.check("gemm_bf16", g_in, g.fetch(), X.expected("gemm_bf16", g_in))
+    X.check("blackscholes", b_in, b.fetch(), X.expected("blackscholes", b_in))
+    rt.close()
