@@ -226,6 +226,11 @@ typedef enum {
                                running (idle or solo phase); otherwise the new
                                kernel waits in R for the next re-plan, which
                                comes when a kernel of the pair runs out */
+#define KL_CFG_RANDOM_PLAN 64u /* the MC comparison of Section 5.1: every re-plan
+                               picks a pair of pending kernel types and a slot
+                               split uniformly at random (counter-based SplitMix64
+                               of kl_config.plan_seed and the phase number)
+                               instead of the largest-CP pair */
 #define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their
@@ -253,6 +258,7 @@ typedef struct {
                                        starved by new arrivals; 0 = 5 ms; ~0 = off.
                                        Batch runs never age (every kernel is present
                                        from the start). */
+    uint64_t plan_seed;             /* KL_CFG_RANDOM_PLAN: seed of the random plans */
 } kl_config;
 
 /* Model inputs for one tenant type (Table 1 parameters, measured by profiling
@@ -438,6 +444,14 @@ int kl_get_model_params(kl_runtime* rt, kl_model_params* out);
 /* CP table the device planner uses: cp[i*KL_T_COUNT+j] and slots for the
  * first kernel of a (type i, type j) pair at `slots` slots per SM. */
 int kl_get_cp_table(kl_runtime* rt, double* cp, uint32_t* slots_a, uint8_t* allowed);
+
+/* Replace the model's table with given values (the OPT comparison of Section
+ * 5.1: the same greedy planner, fed with CPs and slice ratios measured by
+ * running every pair at every split). cp and slots_a as in kl_get_cp_table
+ * (KL_T_COUNT x KL_T_COUNT, host memory, copied); slots_a entries in
+ * [1, slots per SM - 1]; every pair is allowed (no pruning). NULL for both
+ * returns to the model's table. KL_EINVAL on a split out of range. */
+int kl_set_cp_table(kl_runtime* rt, const double* cp, const uint32_t* slots_a);
 
 /* ------------------------------------------------------------ pure functions */
 

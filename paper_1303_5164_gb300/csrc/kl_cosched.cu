@@ -72,6 +72,15 @@ __device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long 
   return v;
 }
 
+// SplitMix64 finaliser (Steele, Lea and Flood 2014; Vigna's constants): the
+// random plans of KL_CFG_RANDOM_PLAN are a function of (seed, phase number).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
 // Co-resident CTAs per SM: 4 x 256 threads at up to 64 registers each.
 constexpr int kCtasPerSm = 4;
 
@@ -264,14 +273,35 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
     for (int t = 0; t < KL_T_COUNT; ++t)
       if (low1[t] >= 0) ph.A = low1[t];
   } else if (npend >= 2) {
+    int32_t aged = -1;
+    // MC comparison (KL_CFG_RANDOM_PLAN): a uniformly random pair of pending
+    // kernel types (the lowest pending kernel of each) and a random split
+    if ((R->flags & KL_CFG_RANDOM_PLAN) && R->slots >= 2) {
+      const unsigned long long r = splitmix64(R->plan_seed ^ (0xD1B54A32D192ED03ull * (seq_old + 1ull)));
+      uint32_t nc = 0;
+      for (int ta = 0; ta < KL_T_COUNT; ++ta)
+        for (int tb = ta; tb < KL_T_COUNT; ++tb)
+          nc += low1[ta] >= 0 && (ta == tb ? low2[ta] >= 0 : low1[tb] >= 0);
+      uint32_t pick = (uint32_t)((r & 0xFFFFFFFFull) % nc);
+      for (int ta = 0; ta < KL_T_COUNT && aged < 0; ++ta)
+        for (int tb = ta; tb < KL_T_COUNT && aged < 0; ++tb) {
+          if (!(low1[ta] >= 0 && (ta == tb ? low2[ta] >= 0 : low1[tb] >= 0))) continue;
+          if (pick-- != 0u) continue;
+          ph.A = min(low1[ta], ta == tb ? low2[ta] : low1[tb]);
+          ph.B = max(low1[ta], ta == tb ? low2[ta] : low1[tb]);
+          ph.slots_a = 1u + (uint32_t)((r >> 32) % (R->slots - 1u));
+          ph.slots_b = R->slots - ph.slots_a;
+          ph.cp = R->cp[tenant(T, R, (uint32_t)ph.A).type][tenant(T, R, (uint32_t)ph.B).type];
+          aged = ph.A;  // a pair is chosen: skip the selections below
+        }
+    }
     // serving: the oldest pending kernel (lowest sequence number) has waited
     // past the age limit: it goes first, with its best partner by CP
-    int32_t aged = -1;
-    if (R->serve && first_pending >= 0 && R->age_limit_ns != ~0ull) {
+    if (aged < 0 && R->serve && first_pending >= 0 && R->age_limit_ns != ~0ull) {
       const unsigned long long ta = __ldcg(&tenant(T, R, (uint32_t)first_pending).t_arrive);
       if (ta != 0ull && gtimer() - ta > R->age_limit_ns) aged = first_pending;
     }
-    if (aged >= 0) {
+    if (aged >= 0 && ph.B < 0) {
       const uint32_t tya = tenant(T, R, (uint32_t)aged).type;
       double best = 0.0;
       int32_t bj = -1;

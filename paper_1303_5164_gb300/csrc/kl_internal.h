@@ -82,6 +82,7 @@ struct alignas(128) RunDev {
   uint32_t chain_slots;        // chain lane: the last chain_slots slots of every SM
   uint32_t pad_s;
   unsigned long long age_limit_ns;    // serving: pending longer than this -> paired first
+  unsigned long long plan_seed;       // KL_CFG_RANDOM_PLAN: seed of the random plans
   unsigned long long wait_limit_ns;
   uint32_t ring_mask;          // tenant slots - 1 (power of two); tenant seq -> slot
   uint32_t phase_mask;         // phase slots - 1 (power of two)

@@ -244,6 +244,7 @@ struct kl_runtime {
   kl_model_params mp{};
   kl_profile prof[KL_T_COUNT];
   bool table_valid = false;
+  bool table_override = false;  // kl_set_cp_table: measured CPs instead of the model
   double cp[KL_T_COUNT][KL_T_COUNT];
   uint32_t slots_a[KL_T_COUNT][KL_T_COUNT];
   uint32_t allowed[KL_T_COUNT][KL_T_COUNT];
@@ -290,6 +291,7 @@ void split_handle(kl_handle h, uint64_t* run, uint32_t* idx) {
 // CP table for every pair of types in `mask` (Section 4.4 model + Section 4.3
 // pruning). Cached until profiles, parameters or the type set change.
 int ensure_table(kl_runtime* rt, uint32_t mask) {
+  if (rt->table_override) return KL_OK;
   if (rt->table_valid && (rt->table_types & mask) == mask) return KL_OK;
   const uint32_t want = mask | (rt->table_valid ? rt->table_types : 0u);
   const uint32_t S = rt->slots;
@@ -904,6 +906,7 @@ static int launch_locked(kl_runtime* rt) {
   R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
   R.flags = rt->cfg.flags;
   R.serve = 0;
+  R.plan_seed = rt->cfg.plan_seed;
   R.chain_slots = std::max(1u, std::min(rt->cfg.chain_slots, rt->slots - 1));
   R.ring_mask = rt->ring_slots - 1;
   R.phase_mask = rt->phase_slots - 1;
@@ -1062,6 +1065,7 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
     R.flags = rt->cfg.flags;
     R.serve = 1;
+    R.plan_seed = rt->cfg.plan_seed;
     R.chain_slots = std::max(1u, std::min(rt->cfg.chain_slots, rt->slots - 1));
     R.age_limit_ns = rt->cfg.age_limit_ns ? rt->cfg.age_limit_ns : 5000000ull;
     R.ring_mask = rt->s_ring - 1u;
@@ -1318,6 +1322,28 @@ extern "C" int kl_get_model_params(kl_runtime* rt, kl_model_params* out) {
   if (!rt || !out) return KL_EINVAL;
   std::lock_guard<std::mutex> lk(rt->mu);
   *out = rt->mp;
+  return KL_OK;
+}
+
+extern "C" int kl_set_cp_table(kl_runtime* rt, const double* cp, const uint32_t* slots_a) {
+  if (!rt || (!cp) != (!slots_a)) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  if (!cp) {
+    rt->table_override = false;
+    rt->table_valid = false;
+    return KL_OK;
+  }
+  for (uint32_t k = 0; k < KL_T_COUNT * KL_T_COUNT; ++k)
+    if (slots_a[k] < 1 || slots_a[k] + 1 > rt->slots || !std::isfinite(cp[k])) return KL_EINVAL;
+  for (uint32_t i = 0; i < KL_T_COUNT; ++i)
+    for (uint32_t j = 0; j < KL_T_COUNT; ++j) {
+      rt->cp[i][j] = cp[i * KL_T_COUNT + j];
+      rt->slots_a[i][j] = slots_a[i * KL_T_COUNT + j];
+      rt->allowed[i][j] = 1;
+    }
+  rt->table_override = true;
+  rt->table_valid = true;
+  rt->table_types = (1u << KL_T_COUNT) - 1u;
   return KL_OK;
 }
 

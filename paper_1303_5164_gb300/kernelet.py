@@ -33,6 +33,7 @@ KL_CFG_CHAIN_LANE = 4
 KL_CFG_SERVE_TC = 8
 KL_CFG_WIDE_FILL = 16
 KL_CFG_LAZY_ARRIVAL = 32
+KL_CFG_RANDOM_PLAN = 64
 
 P = C.c_void_p
 U32, U64, I32, F32, F64 = C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
@@ -104,7 +105,7 @@ class kl_config(C.Structure):
     _fields_ = [("device", I32), ("slots_per_sm", U32), ("max_tenants", U32), ("model_states", U32),
                 ("ratio_policy", U32), ("fixed_slots_a", U32), ("device_wait_limit_ns", U64),
                 ("mem_cap_bytes", U64), ("alpha_p", F64), ("alpha_m", F64), ("flags", U32),
-                ("chain_slots", U32), ("age_limit_ns", U64)]
+                ("chain_slots", U32), ("age_limit_ns", U64), ("plan_seed", U64)]
 
 
 class kl_profile(C.Structure):
@@ -170,6 +171,7 @@ SIGNATURES = [
     ("kl_set_model_params", C.c_int, [P, C.POINTER(kl_model_params)]),
     ("kl_get_model_params", C.c_int, [P, C.POINTER(kl_model_params)]),
     ("kl_get_cp_table", C.c_int, [P, C.POINTER(F64), C.POINTER(U32), C.POINTER(C.c_uint8)]),
+    ("kl_set_cp_table", C.c_int, [P, C.POINTER(F64), C.POINTER(U32)]),
     ("kl_model_ipc", C.c_int, [C.POINTER(kl_model_params), C.POINTER(kl_profile), C.POINTER(U32), U32,
                                U32, C.POINTER(F64)]),
     ("kl_model_pair", C.c_int, [C.POINTER(kl_model_params), C.POINTER(kl_profile), C.POINTER(kl_profile),
@@ -400,3 +402,12 @@ class Runtime:
         al = (C.c_uint8 * (KL_T_COUNT * KL_T_COUNT))()
         check(lib().kl_get_cp_table(self._h, cp, sa, al), "kl_get_cp_table")
         return list(cp), list(sa), list(al)
+
+    def set_cp_table(self, cp=None, slots_a=None):
+        """Override the planner's CP / split table (None: back to the model)."""
+        if cp is None:
+            check(lib().kl_set_cp_table(self._h, None, None), "kl_set_cp_table")
+            return
+        a = (F64 * (KL_T_COUNT * KL_T_COUNT))(*cp)
+        b = (U32 * (KL_T_COUNT * KL_T_COUNT))(*slots_a)
+        check(lib().kl_set_cp_table(self._h, a, b), "kl_set_cp_table")

@@ -239,3 +239,33 @@ def test_tensor_core_build_coschedules_bf16_with_others(K, T):
         for k in g:
             assert X.same_bits(alone[k], g[k]), (t.name, k)
     rt.close()
+
+
+@pytest.mark.parametrize("planner", ["random", "table"])
+def test_other_planners_keep_results(K, T, planner):
+    # the MC comparison's random plans and an overridden CP table change only
+    # the order and sharing of kernels: every result still equals the oracle
+    names = list(MIX_SMALL)
+    inps = [(nm, gen.gen_tenant(nm, 21, i, **MIX_SMALL[nm])) for i, nm in enumerate(names)]
+    c = K.config_default()
+    if planner == "random":
+        c.flags |= K.KL_CFG_RANDOM_PLAN
+        c.plan_seed = 7
+    rt = K.Runtime(c)
+    if planner == "table":
+        n = K.KL_T_COUNT
+        rt.set_cp_table([0.01 * ((i * 7 + j * 3) % 11) for i in range(n) for j in range(n)],
+                        [1 + (i + j) % 3 for i in range(n) for j in range(n)])
+        cp, sa, _ = rt.cp_table()
+        assert sa[1 * n + 2] == 1 + 3 % 3 and abs(cp[2 * n + 5] - 0.01 * ((14 + 15) % 11)) < 1e-15
+    tens = [T.make(nm, x) for nm, x in inps]
+    hs = [rt.submit(t.type, t.args) for t in tens]
+    assert rt.drain() == 0
+    ph = rt.phases()
+    assert any(p.B >= 0 for p in ph)
+    for (nm, x), t, h in zip(inps, tens, hs):
+        assert rt.poll(h) == K.KL_DONE
+        X.check(nm, x, t.fetch(), X.expected(nm, x))
+    if planner == "table":
+        rt.set_cp_table(None)
+    rt.close()
