@@ -83,7 +83,11 @@ typedef enum {
     KL_T_BITONIC = 8,       /* ascending bitonic sort of 2^log2n uint32 keys        */
     KL_T_MATADD = 9,        /* c = a + b on an n x n matrix, 16x16 blocks (Section 4.1 example) */
     KL_T_GEMM_BF16 = 10,    /* C = A B^T, BF16 inputs, FP32 accumulate, tensor cores */
-    KL_T_COUNT = 11
+    KL_T_TEA = 11,          /* Tiny Encryption Algorithm, 32 cycles per 64-bit block */
+    KL_T_SAD = 12,          /* sums of absolute differences, 4x4 blocks, motion search */
+    KL_T_STENCIL = 13,      /* 7-point stencil on a 3-D grid */
+    KL_T_MRIQ = 14,         /* MRI Q matrix: phiMag, then Q over the k-space samples */
+    KL_T_COUNT = 15
 } kl_tenant_type;
 
 /* ----------------------------------------------------------- tenant arguments
@@ -174,6 +178,43 @@ typedef struct {            /* KL_T_GEMM_BF16: one 128x64 tile of C per block  *
     uint32_t M, N, K, pad;
 } kl_args_gemm_bf16;
 
+typedef struct {            /* KL_T_TEA: 512 64-bit blocks per thread block     */
+    const uint32_t* in;     /* [2n] words, block j = (in[2j], in[2j+1]), 16B    */
+    uint32_t* out;          /* [2n] 16B                                         */
+    uint32_t key[4];
+    uint64_t n;             /* 64-bit blocks                                    */
+} kl_args_tea;
+
+typedef struct {            /* KL_T_SAD: 256 SAD values per block               */
+    const uint8_t* cur;     /* [height][width] current frame (8-bit luma)       */
+    const uint8_t* ref;     /* [height][width] reference frame                  */
+    uint32_t* sad;          /* [height/4 * width/4][(2R+1)^2]: for 4x4 block b
+                               (row-major) and displacement (dx, dy) in [-R, R]^2,
+                               index (dy+R)(2R+1) + (dx+R); reference pixels
+                               outside the frame take the nearest edge pixel    */
+    uint32_t width, height; /* multiples of 4                                   */
+    uint32_t range;         /* R, 1..16                                         */
+    uint32_t pad;
+} kl_args_sad;
+
+typedef struct {            /* KL_T_STENCIL: 256 x-points of one (y, z) row per block */
+    const float* in;        /* [nz][ny][nx]                                     */
+    float* out;             /* [nz][ny][nx]; interior: c0 c + c1 (sum of the 6
+                               face neighbours); boundary points copied         */
+    uint32_t nx, ny, nz, pad;
+    float c0, c1;
+} kl_args_stencil;
+
+typedef struct {            /* KL_T_MRIQ: stage 0 = phiMag (256 samples per block),
+                               stage 1 = Q (256 points per block)               */
+    const float *kx, *ky, *kz;  /* [numK] k-space sample coordinates            */
+    const float *phiR, *phiI;   /* [numK]                                        */
+    float* phiMag;              /* [numK] written by stage 0                     */
+    const float *x, *y, *z;     /* [numX] image-space points                    */
+    float *Qr, *Qi;             /* [numX]                                        */
+    uint32_t numK, numX;
+} kl_args_mriq;
+
 /* Launch shape of a tenant as a plain kernel would use it (Section 2.2: a
  * kernel is k thread blocks). Multi-stage tenants (histogram, bitonic sort)
  * are a chain of grids; stage s may start only when stage s-1 has finished. */
@@ -215,10 +256,11 @@ typedef enum {
 #define KL_CFG_FILL_TYPES 2u /* backfill tries the next pending kernels of the two
                                types the co-schedule runs before any other
                                pending kernel; default on */
-#define KL_CFG_SERVE_TC 8u   /* serving runs use the co-scheduler build that can
-                               run KL_T_GEMM_BF16 (tensor cores); without it a
-                               serving run refuses that type (KL_EINVAL). Batch
-                               runs pick the build from the kernels they hold. */
+#define KL_CFG_SERVE_TC 8u   /* serving runs use the full co-scheduler build, which
+                               also runs KL_T_GEMM_BF16 (tensor cores) and the
+                               types after it; without it a serving run refuses
+                               those types (KL_EINVAL). Batch runs pick the build
+                               from the kernels they hold. */
 #define KL_CFG_WIDE_FILL 16u /* backfill considers 8 pending kernels per phase
                                (both chain-lane kernels, then the lowest pending
                                ones) instead of 4; default on */

@@ -10,7 +10,9 @@
  * that are not available; the tenant set below follows the synthetic mix the
  * scheduling experiments need (the co-scheduling method of Section 4 is
  * independent of what a tenant computes, it only needs independent thread
- * blocks, Section 2.2 assumption 2).
+ * blocks, Section 2.2 assumption 2). Four of the paper's kernels are written
+ * here from their textbook definitions: TEA, SAD, the 7-point stencil and
+ * MRI-Q (which adds a sine/cosine recipe, below).
  *
  * Floating point: every float operation is a separately rounded IEEE binary32
  * operation; fused multiply-add appears only where fmaf() is written. Build
@@ -282,4 +284,126 @@ void or_sort_u32(const uint32_t* in, uint32_t* out, int64_t n) {
 
 void or_matadd(const float* a, const float* b, float* c, int64_t n) {
     for (int64_t i = 0; i < n * n; ++i) c[i] = a[i] + b[i];
+}
+
+
+/* ------------------------------------------------------------ TEA */
+/* Tiny Encryption Algorithm (D. Wheeler, R. Needham, "TEA, a Tiny Encryption
+ * Algorithm", FSE 1994): 32 cycles; each cycle adds the key-schedule
+ * constant 0x9E3779B9 to sum, then updates v0 from v1 and v1 from v0, all
+ * modulo 2^32. Block j is (words[2j], words[2j+1]). */
+void or_tea(const uint32_t* words, uint32_t* out, const uint32_t* key, int64_t n) {
+  for (int64_t j = 0; j < n; ++j) {
+    uint32_t v0 = words[2 * j], v1 = words[2 * j + 1], sum = 0;
+    for (int c = 0; c < 32; ++c) {
+      sum += 0x9E3779B9u;
+      v0 += ((v1 << 4) + key[0]) ^ (v1 + sum) ^ ((v1 >> 5) + key[1]);
+      v1 += ((v0 << 4) + key[2]) ^ (v0 + sum) ^ ((v0 >> 5) + key[3]);
+    }
+    out[2 * j] = v0;
+    out[2 * j + 1] = v1;
+  }
+}
+
+/* ------------------------------------------------------------ SAD */
+/* For every 4x4 block (bx, by) of the current frame, in row-major block
+ * order, and every displacement (dx, dy) in [-R, R]^2 (dy major): the sum over
+ * the block's 16 pixels of |cur - ref| with the reference pixel at the
+ * displaced position, coordinates clamped into the frame. */
+void or_sad(const uint8_t* cur, const uint8_t* ref, uint32_t* sad, int64_t W, int64_t H, int64_t R) {
+  const int64_t D = 2 * R + 1;
+  int64_t o = 0;
+  for (int64_t by = 0; by < H / 4; ++by)
+    for (int64_t bx = 0; bx < W / 4; ++bx)
+      for (int64_t dy = -R; dy <= R; ++dy)
+        for (int64_t dx = -R; dx <= R; ++dx) {
+          uint32_t acc = 0;
+          for (int64_t i = 0; i < 4; ++i)
+            for (int64_t j = 0; j < 4; ++j) {
+              int64_t y = 4 * by + i, x = 4 * bx + j;
+              int64_t ry = y + dy < 0 ? 0 : (y + dy > H - 1 ? H - 1 : y + dy);
+              int64_t rx = x + dx < 0 ? 0 : (x + dx > W - 1 ? W - 1 : x + dx);
+              int d = (int)cur[y * W + x] - (int)ref[ry * W + rx];
+              acc += (uint32_t)(d < 0 ? -d : d);
+            }
+          sad[o++] = acc;
+        }
+  (void)D;
+}
+
+/* ------------------------------------------------------------ 3-D stencil */
+/* 7-point stencil on an nz x ny x nx grid (x fastest): interior points
+ * c0 * c + c1 * s with s = ((((w + e) + n) + s) + b) + t over the six face
+ * neighbours (-x, +x, -y, +y, -z, +z), each addition rounded, then
+ * fmaf(c1, s, c0 * c); points on the grid's faces are copied. */
+void or_stencil7(const float* in, float* out, int64_t nx, int64_t ny, int64_t nz, float c0, float c1) {
+  const int64_t sy = nx, sz = nx * ny;
+  for (int64_t z = 0; z < nz; ++z)
+    for (int64_t y = 0; y < ny; ++y)
+      for (int64_t x = 0; x < nx; ++x) {
+        const int64_t i = z * sz + y * sy + x;
+        if (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1) {
+          out[i] = in[i];
+          continue;
+        }
+        float s = in[i - 1] + in[i + 1];
+        s = s + in[i - sy];
+        s = s + in[i + sy];
+        s = s + in[i - sz];
+        s = s + in[i + sz];
+        out[i] = fmaf(c1, s, c0 * in[i]);
+      }
+}
+
+/* ------------------------------------------------------------ MRI-Q */
+/* sine and cosine of a binary32 angle: Cody-Waite reduction a = n pi/2 + r
+ * with pi/2 in two parts (1.57079637f, -4.37113900e-8f) and n the nearest
+ * integer to a * 2/pi; Taylor polynomials of sin (to r^9) and cos (to r^8)
+ * on |r| <= pi/4 in Horner form with fmaf; the quadrant n mod 4 swaps and
+ * negates them. */
+void or_sincosf(float a, float* sn, float* cs) {
+  const float n = rintf(a * 0.636619772f);
+  float r = fmaf(-n, 1.57079637f, a);
+  r = fmaf(-n, -4.37113900e-8f, r);
+  const float r2 = r * r;
+  float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);
+  ps = fmaf(r2, ps, 8.33333333e-3f);
+  ps = fmaf(r2, ps, -1.66666667e-1f);
+  const float s = fmaf(r * r2, ps, r);
+  float pc = fmaf(r2, 2.48015873e-5f, -1.38888889e-3f);
+  pc = fmaf(r2, pc, 4.16666667e-2f);
+  pc = fmaf(r2, pc, -0.5f);
+  const float c = fmaf(r2, pc, 1.0f);
+  switch (((int)n) & 3) {
+    case 0: *sn = s; *cs = c; break;
+    case 1: *sn = c; *cs = -s; break;
+    case 2: *sn = -s; *cs = -c; break;
+    default: *sn = -c; *cs = s; break;
+  }
+}
+
+/* phiMag[k] = fmaf(phiI, phiI, phiR * phiR); for each point x:
+ * Qr = sum_k phiMag[k] cos(2 pi (k . x)), Qi likewise with sin, k ascending,
+ * each term fmaf(phiMag, cos, Qr); k . x = fmaf(kz, z, fmaf(ky, y, kx * x));
+ * the angle is 6.28318548f (binary32 2 pi) times it, rounded.
+ * Points [lo, hi) only, so tests can sample large cases. */
+void or_mriq(const float* kx, const float* ky, const float* kz, const float* phiR, const float* phiI,
+             float* phiMag, const float* x, const float* y, const float* z, float* Qr, float* Qi, int64_t numK,
+             const int64_t* pts, int64_t npts) {
+  for (int64_t k = 0; k < numK; ++k) phiMag[k] = fmaf(phiI[k], phiI[k], phiR[k] * phiR[k]);
+  for (int64_t p = 0; p < npts; ++p) {
+    const int64_t i = pts[p];
+    float qr = 0.0f, qi = 0.0f;
+    for (int64_t k = 0; k < numK; ++k) {
+      float t = kx[k] * x[i];
+      t = fmaf(ky[k], y[i], t);
+      t = fmaf(kz[k], z[i], t);
+      float sn, cs;
+      or_sincosf(6.28318548f * t, &sn, &cs);
+      qr = fmaf(phiMag[k], cs, qr);
+      qi = fmaf(phiMag[k], sn, qi);
+    }
+    Qr[p] = qr;
+    Qi[p] = qi;
+  }
 }

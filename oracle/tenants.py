@@ -51,6 +51,12 @@ def lib():
         _lib.or_escape.argtypes = [u32p, L, L, L, C.c_float, C.c_float, C.c_float, C.c_float, L, L]
         _lib.or_sort_u32.argtypes = [u32p, u32p, L]
         _lib.or_matadd.argtypes = [f32p, f32p, f32p, L]
+        _lib.or_tea.argtypes = [u32p, u32p, u32p, L]
+        _lib.or_sad.argtypes = [u8p, u8p, u32p, L, L, L]
+        _lib.or_stencil7.argtypes = [f32p, f32p, L, L, L, C.c_float, C.c_float]
+        fp = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+        _lib.or_sincosf.argtypes = [C.c_float, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+        _lib.or_mriq.argtypes = [f32p] * 11 + [L, i64p, L]
     return _lib
 
 
@@ -177,3 +183,41 @@ def matadd(a, b):
     c = np.empty((n, n), np.float32)
     lib().or_matadd(_c(a, np.float32), _c(b, np.float32), c, n)
     return c
+
+
+def tea(words, key, n):
+    out = np.empty(2 * n, np.uint32)
+    lib().or_tea(_c(words, np.uint32), out, _c(key, np.uint32), n)
+    return out
+
+
+def sad(cur, ref, width, height, rng):
+    D = 2 * rng + 1
+    out = np.empty((width // 4) * (height // 4) * D * D, np.uint32)
+    lib().or_sad(_c(cur, np.uint8), _c(ref, np.uint8), out, width, height, rng)
+    return out
+
+
+def stencil7(grid, nx, ny, nz, c0, c1):
+    out = np.empty(nx * ny * nz, np.float32)
+    lib().or_stencil7(_c(grid, np.float32), out, nx, ny, nz, float(c0), float(c1))
+    return out
+
+
+def sincosf(a):
+    s, c = C.c_float(), C.c_float()
+    lib().or_sincosf(float(a), C.byref(s), C.byref(c))
+    return s.value, c.value
+
+
+def mriq(inp, points=None):
+    """phiMag for every sample and (Qr, Qi) at `points` (default: every point)."""
+    numK, numX = inp["numK"], inp["numX"]
+    pts = np.arange(numX, dtype=np.int64) if points is None else np.asarray(points, np.int64)
+    pm = np.empty(numK, np.float32)
+    qr = np.empty(len(pts), np.float32)
+    qi = np.empty(len(pts), np.float32)
+    f = lambda k: _c(inp[k], np.float32)
+    lib().or_mriq(f("kx"), f("ky"), f("kz"), f("phiR"), f("phiI"), pm, f("x"), f("y"), f("z"), qr, qi, numK,
+                  _c(pts, np.int64), len(pts))
+    return pm, qr, qi

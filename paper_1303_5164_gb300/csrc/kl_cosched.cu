@@ -114,6 +114,19 @@ __device__ __forceinline__ PhaseDev* phase(PhaseDev* P, const RunDev* R, uint32_
 // position among the slots of its SM that serve t: while the stage has fewer
 // blocks left than rank * numSM, the slot leaves them to lower ranks, so a
 // kernel with few blocks spreads one per SM instead of stacking on some SMs.
+// Stage containing cumulative block g, from the descriptor's block counts
+// (no argument parsing on the scheduler's path).
+__device__ __forceinline__ tn::Stage stage_at(const TenantDev& d, uint32_t type, uint32_t g) {
+  const uint32_t total = d.total, b0 = d.blocks0;
+  if (d.nstages == 1u) return tn::Stage{0u, 0u, total};
+  if (type == KL_T_BITONIC) {
+    const uint32_t s = g / b0;
+    return tn::Stage{s, s * b0, (s + 1u) * b0};
+  }
+  return g < b0 ? tn::Stage{0u, 0u, b0} : tn::Stage{1u, b0, total};
+}
+
+template <bool TC>
 __device__ __forceinline__ int try_pull(TenantDev* T, const RunDev* R, int32_t t, uint32_t rank, uint32_t n_sm,
                                         uint32_t& g0, uint32_t& g1) {
   TenantDev& d = tenant(T, R, (uint32_t)t);
@@ -122,7 +135,7 @@ __device__ __forceinline__ int try_pull(TenantDev* T, const RunDev* R, int32_t t
   const uint32_t total = d.total;
   uint32_t n = ld_relaxed(&d.next);
   if (n >= total) return kExhausted;
-  tn::Stage st = tn::stage_of(d.type, d.args, n);
+  tn::Stage st = stage_at(d, d.type, n);
   if (st.begin > ld_relaxed(&d.done)) return kBlocked;  // previous stage still running
   if ((uint64_t)rank * n_sm >= (uint64_t)(st.end - n)) return kBlocked;
   uint32_t a = atomicAdd(&d.next, d.slice);
@@ -593,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
               const int32_t c = __ldcg(&pp->chain[f]);
               if (c < 0) break;
               uint32_t g0 = 0, g1 = 0;
-              if (try_pull(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
+              if (try_pull<TC>(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
                 ctl.action = kActRun;
                 ctl.tenant = c;
                 ctl.g0 = g0;
@@ -609,7 +622,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
             const uint32_t rank1 = mine_is_b ? slot - ph.slots_a : slot;
             const uint32_t rank2 = mine_is_b ? slot : slot + (S - ph.slots_a);
             uint32_t g0 = 0, g1 = 0;
-            int r = try_pull(T, R, t1, rank1, n_sm, g0, g1);
+            int r = try_pull<TC>(T, R, t1, rank1, n_sm, g0, g1);
             if (r == kPulled) {
               ctl.action = kActRun;
               ctl.tenant = t1;
@@ -627,7 +640,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
                 ctl.seq = seq;
                 ctl.trigger = trig;
               } else if (t2 >= 0) {
-                int r2 = try_pull(T, R, t2, rank2, n_sm, g0, g1);
+                int r2 = try_pull<TC>(T, R, t2, rank2, n_sm, g0, g1);
                 if (r2 == kPulled) {
                   ctl.action = kActRun;
                   ctl.tenant = t2;
@@ -654,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
               const int32_t c = __ldcg(&pp->fill[f]);
               if (c < 0) break;
               uint32_t g0 = 0, g1 = 0;
-              if (try_pull(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
+              if (try_pull<TC>(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
                 ctl.action = kActRun;
                 ctl.tenant = c;
                 ctl.g0 = g0;
@@ -696,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
       uint32_t g = ctl.g0;
       const uint32_t g1 = ctl.g1;
       while (g < g1) {
-        const tn::Stage st = tn::stage_of(type, d.args, g);
+        const tn::Stage st = stage_at(d, type, g);
         if (st.begin > 0) {
           // the previous stage must be complete before any block of this one runs
           if (tid == 0) {

@@ -21,7 +21,8 @@ struct alignas(128) TenantDev {
   uint32_t total;         // thread blocks summed over stages
   uint32_t nstages;
   uint32_t index;         // submit index within the run
-  uint32_t pad0;
+  uint32_t blocks0;       // blocks of stage 0 (stages after it: equal size for the bitonic sort,
+                          // one more stage holding the rest otherwise)
   unsigned long long t_arrive;  // serving: globaltimer when the device took the kernel in
   alignas(16) unsigned char args[KL_MAX_ARGS_BYTES];
   // ---- dynamic (own 128-byte line, away from the arguments)

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) native_kernel(ArgsBlob args, uint32_
   const tn::Stage st{stage, 0u, 0u};
   const tn::BlockCtx cx{&s_tmem, &g_native_error, 2000000000ull};
   if constexpr (TYPE == KL_T_GEMM_BF16) tn::acquire_tmem(cx);
-  tn::run_block<TYPE == KL_T_GEMM_BF16>(TYPE, args.b, st, blockIdx.x, smem, cx);
+  tn::run_block<!tn::in_plain_build(TYPE)>(TYPE, args.b, st, blockIdx.x, smem, cx);
   if constexpr (TYPE == KL_T_GEMM_BF16) tn::release_tmem(cx);
 }
 
@@ -61,6 +61,10 @@ int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s) {
       case KL_T_BITONIC: e = launch_one<KL_T_BITONIC>(args, st, nb, s); break;
       case KL_T_MATADD: e = launch_one<KL_T_MATADD>(args, st, nb, s); break;
       case KL_T_GEMM_BF16: e = launch_one<KL_T_GEMM_BF16>(args, st, nb, s); break;
+      case KL_T_TEA: e = launch_one<KL_T_TEA>(args, st, nb, s); break;
+      case KL_T_SAD: e = launch_one<KL_T_SAD>(args, st, nb, s); break;
+      case KL_T_STENCIL: e = launch_one<KL_T_STENCIL>(args, st, nb, s); break;
+      case KL_T_MRIQ: e = launch_one<KL_T_MRIQ>(args, st, nb, s); break;
       default: return -1;
     }
     if (e != cudaSuccess) return -1;

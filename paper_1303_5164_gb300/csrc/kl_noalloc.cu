@@ -104,6 +104,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
     t.type = d.type;
     t.total = (uint32_t)sh.total_blocks;
     t.nstages = sh.nstages;
+    t.blocks0 = sh.grid[0];
     t.index = i;
     // a slice never exceeds the kernel, and the queue counter (which can
     // overshoot by one slice per CTA when a kernel runs out) stays below 2^32
@@ -141,7 +142,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
       cudaMemcpyAsync(dP, &img.ph0, sizeof(PhaseDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return KL_ECUDA;
   bool tc = false;
-  for (uint32_t i = 0; i < n; ++i) tc |= descs[i].type == KL_T_GEMM_BF16;
+  for (uint32_t i = 0; i < n; ++i) tc |= !tn::in_plain_build(descs[i].type);
   if (cosched_launch(dT, dR, dP, n_sm, S, tn::kMaxTenantSmem, tc, s) != 0) return KL_ECUDA;
   if (cudaMemcpyAsync(img.t, dT, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&img.run, dR, sizeof(RunDev), cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -63,6 +63,10 @@ size_t args_size_of(uint32_t type) {
     case KL_T_BITONIC: return sizeof(kl_args_bitonic);
     case KL_T_MATADD: return sizeof(kl_args_matadd);
     case KL_T_GEMM_BF16: return sizeof(kl_args_gemm_bf16);
+    case KL_T_TEA: return sizeof(kl_args_tea);
+    case KL_T_SAD: return sizeof(kl_args_sad);
+    case KL_T_STENCIL: return sizeof(kl_args_stencil);
+    case KL_T_MRIQ: return sizeof(kl_args_mriq);
     default: return 0;
   }
 }
@@ -130,6 +134,30 @@ int validate_args(uint32_t type, const void* a) {
         return KL_EINVAL;
       return KL_OK;
     }
+    case KL_T_TEA: {
+      const kl_args_tea* t = (const kl_args_tea*)a;
+      if (!t->in || !t->out || t->n == 0 || !a16(t->in) || !a16(t->out)) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_SAD: {
+      const kl_args_sad* d = (const kl_args_sad*)a;
+      if (!d->cur || !d->ref || !d->sad || d->width < 4 || d->height < 4 || d->width % 4 || d->height % 4 ||
+          d->range < 1 || d->range > 16)
+        return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_STENCIL: {
+      const kl_args_stencil* t = (const kl_args_stencil*)a;
+      if (!t->in || !t->out || t->nx == 0 || t->ny == 0 || t->nz == 0) return KL_EINVAL;
+      return KL_OK;
+    }
+    case KL_T_MRIQ: {
+      const kl_args_mriq* m = (const kl_args_mriq*)a;
+      if (!m->kx || !m->ky || !m->kz || !m->phiR || !m->phiI || !m->phiMag || !m->x || !m->y || !m->z || !m->Qr ||
+          !m->Qi || m->numK == 0 || m->numX == 0)
+        return KL_EINVAL;
+      return KL_OK;
+    }
     default: return KL_EINVAL;
   }
 }
@@ -150,6 +178,10 @@ uint32_t default_slice(uint32_t type) {
     case KL_T_BITONIC: return 2;
     case KL_T_MATADD: return 8;
     case KL_T_GEMM_BF16: return 1;
+    case KL_T_TEA: return 4;
+    case KL_T_SAD: return 8;
+    case KL_T_STENCIL: return 4;
+    case KL_T_MRIQ: return 1;
     default: return 1;
   }
 }
@@ -175,6 +207,10 @@ kl_profile builtin_profile(uint32_t type) {
     case KL_T_BITONIC: p.R_m = 0.10; p.f_u = 0.0; p.L0 = 500; p.I_block = 8 * 400; p.PUR = 0.30; p.MUR = 0.30; break;
     case KL_T_MATADD: p.R_m = 0.25; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 12; p.PUR = 0.05; p.MUR = 0.70; break;
     case KL_T_GEMM_BF16: p.R_m = 0.02; p.f_u = 0.0; p.L0 = 700; p.I_block = 8 * 200; p.PUR = 0.10; p.MUR = 0.10; break;
+    case KL_T_TEA: p.R_m = 0.002; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 1600; p.PUR = 0.90; p.MUR = 0.05; break;
+    case KL_T_SAD: p.R_m = 0.25; p.f_u = 0.3; p.L0 = 500; p.I_block = 8 * 150; p.PUR = 0.40; p.MUR = 0.10; break;
+    case KL_T_STENCIL: p.R_m = 0.2; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 60; p.PUR = 0.20; p.MUR = 0.60; break;
+    case KL_T_MRIQ: p.R_m = 0.001; p.f_u = 0.0; p.L0 = 500; p.I_block = 8 * 20000; p.PUR = 0.85; p.MUR = 0.01; break;
     default: p.valid = 0; break;
   }
   return p;
@@ -603,7 +639,7 @@ int serve_publish(kl_runtime* rt, TenantDev td, uint64_t footprint, kl_handle* o
   if (!rt->in_flight || (rt->kind != kServe && rt->kind != kServeBase)) return KL_ESTATE;  // the run has ended
   if (rt->kind == kServeBase && rt->s_joined) return KL_ESTATE;
   if (rt->kind == kServe && __atomic_load_n(&rt->sm_ctl[32], __ATOMIC_RELAXED)) return KL_ESTATE;  // stopping
-  if (rt->kind == kServe && td.type == KL_T_GEMM_BF16 && !(rt->cfg.flags & KL_CFG_SERVE_TC)) return KL_EINVAL;
+  if (rt->kind == kServe && !tn::in_plain_build(td.type) && !(rt->cfg.flags & KL_CFG_SERVE_TC)) return KL_EINVAL;
   if (rt->s_inflight >= rt->cap) return KL_EAGAIN;
   if (rt->cfg.mem_cap_bytes && rt->s_footprint + footprint > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
   const uint32_t seq = rt->s_tail;
@@ -867,6 +903,7 @@ extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out
                                               : default_slice(d->type);
   td.total = (uint32_t)sh.total_blocks;
   td.nstages = sh.nstages;
+  td.blocks0 = sh.grid[0];
   memcpy(td.args, d->args, d->args_size);
   if (rt->serve_on) return serve_publish(rt, td, d->footprint_bytes, out);
   if (rt->pending.size() >= rt->cap) return KL_EAGAIN;
@@ -930,7 +967,7 @@ static int launch_locked(kl_runtime* rt) {
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_phases, rt->h_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
-  const bool tc = (mask >> KL_T_GEMM_BF16) & 1u;
+  const bool tc = (mask >> (KL_T_MATADD + 1)) != 0u;  // any type outside the plain build
   if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, rt->slots, smem, tc, s) != 0)
     rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
@@ -1092,7 +1129,7 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     const bool tc = (rt->cfg.flags & KL_CFG_SERVE_TC) != 0;
     uint32_t smem = tn::kMinCtaSmem;
     for (uint32_t t = 0; t < KL_T_COUNT; ++t)
-      if (t != KL_T_GEMM_BF16 || tc) smem = std::max(smem, tn::smem_bytes(t));
+      if (tn::in_plain_build(t) || tc) smem = std::max(smem, tn::smem_bytes(t));
     if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, smem, tc, s) != 0)
       rc = KL_ECUDA;
     if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));

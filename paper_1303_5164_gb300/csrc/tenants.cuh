@@ -56,6 +56,10 @@ constexpr uint32_t kBfStageB = kBfBN * kBfBK * 2u;      // 8 KB
 constexpr uint32_t kBfStage = kBfStageA + kBfStageB;
 constexpr uint32_t kBfSmem = 1024u + 2u * kBfStage + 64u;  // alignment slack, stages, barriers
 constexpr uint32_t kBfTmemCols = 64;                       // FP32 accumulator: 128 lanes x 64 columns
+constexpr int kTeaPerBlock = 512;        // 64-bit blocks (two per thread, one 16-byte load)
+constexpr int kSadPerBlock = 256;        // SAD values (one per thread)
+constexpr int kStencilPerBlock = 256;    // x-points of one row
+constexpr int kMriqPerBlock = 256;       // k-samples (stage 0) or image points (stage 1)
 
 __host__ __device__ inline uint32_t bitonic_tile_log2(uint32_t L) {
   return L < (uint32_t)kBitonicTileLog2 ? L : (uint32_t)kBitonicTileLog2;
@@ -71,6 +75,7 @@ __host__ __device__ inline uint32_t bitonic_nstages(uint32_t L) {
 __host__ __device__ inline uint32_t nstages(uint32_t type, const void* a) {
   switch (type) {
     case KL_T_HIST256: return 2;
+    case KL_T_MRIQ: return 2;
     case KL_T_BITONIC: return bitonic_nstages(((const kl_args_bitonic*)a)->log2n);
     default: return 1;
   }
@@ -104,6 +109,20 @@ __host__ __device__ inline uint32_t stage_blocks(uint32_t type, const void* a, u
       const kl_args_gemm_bf16* g = (const kl_args_gemm_bf16*)a;
       return cdiv64(g->M, kBfBM) * cdiv64(g->N, kBfBN);
     }
+    case KL_T_TEA: return cdiv64(((const kl_args_tea*)a)->n, kTeaPerBlock);
+    case KL_T_SAD: {
+      const kl_args_sad* d = (const kl_args_sad*)a;
+      const uint64_t D = 2ull * d->range + 1ull;
+      return cdiv64((uint64_t)(d->width / 4) * (d->height / 4) * D * D, kSadPerBlock);
+    }
+    case KL_T_STENCIL: {
+      const kl_args_stencil* t = (const kl_args_stencil*)a;
+      return cdiv64(t->nx, kStencilPerBlock) * t->ny * t->nz;
+    }
+    case KL_T_MRIQ: {
+      const kl_args_mriq* m = (const kl_args_mriq*)a;
+      return s == 0 ? cdiv64(m->numK, kMriqPerBlock) : cdiv64(m->numX, kMriqPerBlock);
+    }
     default: return 0;
   }
 }
@@ -127,8 +146,17 @@ __host__ __device__ inline Stage stage_of(uint32_t type, const void* a, uint32_t
     uint32_t s = g / nb;
     return Stage{s, s * nb, (s + 1) * nb};
   }
+  if (type == KL_T_MRIQ) {
+    const uint32_t n0 = stage_blocks(type, a, 0);
+    if (g < n0) return Stage{0, 0, n0};
+    return Stage{1, n0, n0 + stage_blocks(type, a, 1)};
+  }
   return Stage{0, 0, stage_blocks(type, a, 0)};
 }
+
+
+// Types the plain co-scheduler build runs; the others need the full build.
+__host__ __device__ constexpr bool in_plain_build(uint32_t type) { return type <= KL_T_MATADD; }
 
 __host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
   switch (type) {
@@ -137,6 +165,7 @@ __host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
     case KL_T_HIST256: return 256u * 32u * 4u;                                    // 32 KB
     case KL_T_BITONIC: return ((1u << kBitonicTileLog2) + (1u << (kBitonicTileLog2 - 5))) * 4u;  // padded tile
     case KL_T_GEMM_BF16: return kBfSmem;                                          // 49.1 KB
+    case KL_T_MRIQ: return 4u * kMriqPerBlock * 4u;                               // 4 KB k-sample chunk
     default: return 0;
   }
 }
@@ -880,6 +909,168 @@ __device__ __forceinline__ void matadd_block(const kl_args_matadd& a, uint32_t v
   a.c[i] = __fadd_rn(a.a[i], a.b[i]);
 }
 
+// ------------------------------------------------------------------ TEA
+// Tiny Encryption Algorithm (Wheeler and Needham, 1994): 32 cycles of the
+// Feistel round on the 64-bit block (v0, v1) with the 128-bit key; integer
+// arithmetic modulo 2^32. Two blocks per thread from one 16-byte load.
+
+__device__ __forceinline__ void tea_encrypt(uint32_t& v0, uint32_t& v1, const uint32_t (&k)[4]) {
+  uint32_t sum = 0u;
+#pragma unroll 8
+  for (int r = 0; r < 32; ++r) {
+    sum += 0x9E3779B9u;  // the cipher's key-schedule constant
+    v0 += ((v1 << 4) + k[0]) ^ (v1 + sum) ^ ((v1 >> 5) + k[1]);
+    v1 += ((v0 << 4) + k[2]) ^ (v0 + sum) ^ ((v0 >> 5) + k[3]);
+  }
+}
+
+__device__ __forceinline__ void tea_block(const kl_args_tea& a, uint32_t vb) {
+  const uint32_t k[4] = {a.key[0], a.key[1], a.key[2], a.key[3]};
+  const uint64_t j = (uint64_t)vb * kTeaPerBlock + 2u * threadIdx.x;  // first of this thread's two blocks
+  if (j + 1 < a.n) {
+    uint4 w = reinterpret_cast<const uint4*>(a.in)[j >> 1];
+    tea_encrypt(w.x, w.y, k);
+    tea_encrypt(w.z, w.w, k);
+    reinterpret_cast<uint4*>(a.out)[j >> 1] = w;
+  } else if (j < a.n) {
+    uint32_t v0 = a.in[2 * j], v1 = a.in[2 * j + 1];
+    tea_encrypt(v0, v1, k);
+    a.out[2 * j] = v0;
+    a.out[2 * j + 1] = v1;
+  }
+}
+
+// ------------------------------------------------------------------ SAD
+// Sums of absolute differences for motion estimation: thread o computes the
+// SAD of 4x4 block b = o / D^2 of the current frame against the reference
+// frame displaced by (dx, dy) = (o mod D - R, (o / D) mod D - R), D = 2R + 1,
+// reference coordinates clamped to the frame.
+
+__device__ __forceinline__ void sad_block(const kl_args_sad& a, uint32_t vb) {
+  const uint32_t D = 2u * a.range + 1u, D2 = D * D;
+  const uint32_t mbw = a.width / 4u;
+  const uint64_t o = (uint64_t)vb * kSadPerBlock + threadIdx.x;
+  const uint64_t nout = (uint64_t)mbw * (a.height / 4u) * D2;
+  if (o >= nout) return;
+  const uint32_t b = (uint32_t)(o / D2), d = (uint32_t)(o % D2);
+  const int dy = (int)(d / D) - (int)a.range, dx = (int)(d % D) - (int)a.range;
+  const int x0 = (int)(4u * (b % mbw)), y0 = (int)(4u * (b / mbw));
+  const int W = (int)a.width, H = (int)a.height;
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ry = min(max(y0 + i + dy, 0), H - 1);
+    const uint8_t* crow = a.cur + (size_t)(y0 + i) * W + x0;
+    const uint8_t* rrow = a.ref + (size_t)ry * W;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int rx = min(max(x0 + j + dx, 0), W - 1);
+      const int c = __ldg(crow + j), r = __ldg(rrow + rx);
+      acc += (uint32_t)abs(c - r);
+    }
+  }
+  a.sad[o] = acc;
+}
+
+// ------------------------------------------------------------------ 3-D stencil
+// 7-point stencil: an interior point becomes c0 * c + c1 * s with s the sum of
+// its six face neighbours added in the order -x, +x, -y, +y, -z, +z (each sum
+// rounded, then one fused multiply-add); boundary points are copied.
+
+__device__ __forceinline__ void stencil_block(const kl_args_stencil& a, uint32_t vb) {
+  const uint32_t bpr = (a.nx + kStencilPerBlock - 1) / kStencilPerBlock;
+  const uint32_t row = vb / bpr;
+  const uint32_t x = (vb % bpr) * kStencilPerBlock + threadIdx.x;
+  if (x >= a.nx) return;
+  const uint32_t y = row % a.ny, z = row / a.ny;
+  const uint64_t sx = 1, sy = a.nx, sz = (uint64_t)a.nx * a.ny;
+  const uint64_t i = (uint64_t)z * sz + (uint64_t)y * sy + x;
+  const float c = __ldg(a.in + i);
+  if (x == 0 || y == 0 || z == 0 || x + 1 == a.nx || y + 1 == a.ny || z + 1 == a.nz) {
+    a.out[i] = c;
+    return;
+  }
+  float s = __fadd_rn(__ldg(a.in + i - sx), __ldg(a.in + i + sx));
+  s = __fadd_rn(s, __ldg(a.in + i - sy));
+  s = __fadd_rn(s, __ldg(a.in + i + sy));
+  s = __fadd_rn(s, __ldg(a.in + i - sz));
+  s = __fadd_rn(s, __ldg(a.in + i + sz));
+  a.out[i] = __fmaf_rn(a.c1, s, __fmul_rn(a.c0, c));
+}
+
+// ------------------------------------------------------------------ MRI-Q
+// Q of an MRI reconstruction: stage 0 phiMag[k] = phiR^2 + phiI^2 (one fused
+// multiply-add on the rounded square of phiR); stage 1 for every image point
+// x: Qr = sum_k phiMag[k] cos(2 pi (k . x)), Qi = sum_k phiMag[k] sin(...),
+// k ascending, each term one fused multiply-add. The dot product is
+// kx*x, then fused ky*y and kz*z; the angle is its rounded product with the
+// binary32 nearest to 2 pi. Sine and cosine: Cody-Waite reduction by pi/2 with
+// a two-part constant, then Taylor polynomials (degree 9 for sine, 8 for
+// cosine) on [-pi/4, pi/4] in Horner form with fused multiply-adds, and the
+// quadrant's sign and swap.
+
+__device__ __forceinline__ void kl_sincosf(float a, float& sn, float& cs) {
+  const float n = rintf(__fmul_rn(a, 0.636619772f));  // a * 2/pi, nearest integer
+  float r = __fmaf_rn(-n, 1.57079637f, a);            // pi/2 split: 1.57079637f + (-4.37113900e-8f)
+  r = __fmaf_rn(-n, -4.37113900e-8f, r);
+  const float r2 = __fmul_rn(r, r);
+  float ps = __fmaf_rn(r2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
+  ps = __fmaf_rn(r2, ps, 8.33333333e-3f);                        // 1/5!
+  ps = __fmaf_rn(r2, ps, -1.66666667e-1f);                       // -1/3!
+  const float s = __fmaf_rn(__fmul_rn(r, r2), ps, r);
+  float pc = __fmaf_rn(r2, 2.48015873e-5f, -1.38888889e-3f);     // 1/8!, -1/6!
+  pc = __fmaf_rn(r2, pc, 4.16666667e-2f);                        // 1/4!
+  pc = __fmaf_rn(r2, pc, -0.5f);                                 // -1/2!
+  const float c = __fmaf_rn(r2, pc, 1.0f);
+  const int q = ((int)n) & 3;
+  sn = q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
+  cs = q == 0 ? c : q == 1 ? -s : q == 2 ? -c : s;
+}
+
+__device__ __forceinline__ void mriq_block(const kl_args_mriq& a, uint32_t stage, uint32_t vb, char* smem) {
+  if (stage == 0) {
+    const uint32_t k = vb * kMriqPerBlock + threadIdx.x;
+    if (k < a.numK) {
+      const float r = __ldg(a.phiR + k), im = __ldg(a.phiI + k);
+      a.phiMag[k] = __fmaf_rn(im, im, __fmul_rn(r, r));
+    }
+    return;
+  }
+  float* s_kx = reinterpret_cast<float*>(smem);
+  float* s_ky = s_kx + kMriqPerBlock;
+  float* s_kz = s_ky + kMriqPerBlock;
+  float* s_pm = s_kz + kMriqPerBlock;
+  const uint32_t xi = vb * kMriqPerBlock + threadIdx.x;
+  const bool live = xi < a.numX;
+  const float px = live ? __ldg(a.x + xi) : 0.f, py = live ? __ldg(a.y + xi) : 0.f, pz = live ? __ldg(a.z + xi) : 0.f;
+  float qr = 0.f, qi = 0.f;
+  for (uint32_t k0 = 0; k0 < a.numK; k0 += kMriqPerBlock) {
+    const uint32_t k = k0 + threadIdx.x;
+    __syncthreads();
+    if (k < a.numK) {
+      s_kx[threadIdx.x] = __ldg(a.kx + k);
+      s_ky[threadIdx.x] = __ldg(a.ky + k);
+      s_kz[threadIdx.x] = __ldg(a.kz + k);
+      s_pm[threadIdx.x] = a.phiMag[k];  // written by stage 0 of this kernel: not through the read-only path
+    }
+    __syncthreads();
+    const uint32_t kn = min((uint32_t)kMriqPerBlock, a.numK - k0);
+    for (uint32_t j = 0; j < kn; ++j) {
+      float t = __fmul_rn(s_kx[j], px);
+      t = __fmaf_rn(s_ky[j], py, t);
+      t = __fmaf_rn(s_kz[j], pz, t);
+      float sn, cs;
+      kl_sincosf(__fmul_rn(6.28318548f, t), sn, cs);
+      qr = __fmaf_rn(s_pm[j], cs, qr);
+      qi = __fmaf_rn(s_pm[j], sn, qi);
+    }
+  }
+  if (live) {
+    a.Qr[xi] = qr;
+    a.Qi[xi] = qi;
+  }
+}
+
 // ------------------------------------------------------------------ BF16 GEMM on tensor cores
 // C[M][N] = sum_k A[m][k] * Bt[n][k], A and Bt bfloat16 (both K-major), FP32
 // accumulation in tensor memory. Per block (one 128x64 tile of C): thread 0
@@ -1110,9 +1301,11 @@ __device__ __forceinline__ A load_args(const void* p) {
   return *reinterpret_cast<const A*>(p);
 }
 
-// TC: whether this caller is built with the tensor-core tenant. Any tcgen05
-// instruction in a kernel makes the CUDA occupancy calculator allow one CTA
-// per SM, so kernels that never run the BF16 GEMM are built without it.
+// TC: whether this caller is the full build: the tensor-core tenant and the
+// types after it (TEA, SAD, stencil, MRI-Q). Any tcgen05 instruction in a
+// kernel makes the CUDA occupancy calculator allow one CTA per SM, and every
+// extra body adds register pressure to the shared 64-register budget, so the
+// plain build (the first ten types) carries neither.
 template <bool TC>
 __device__ __forceinline__ void run_block(uint32_t type, const void* args, const Stage& st, uint32_t g,
                                           char* smem, const BlockCtx& cx) {
@@ -1130,6 +1323,18 @@ __device__ __forceinline__ void run_block(uint32_t type, const void* args, const
     case KL_T_MATADD: matadd_block(load_args<kl_args_matadd>(args), vb); break;
     case KL_T_GEMM_BF16:
       if constexpr (TC) gemm_bf16_block(load_args<kl_args_gemm_bf16>(args), vb, smem, cx);
+      break;
+    case KL_T_TEA:
+      if constexpr (TC) tea_block(load_args<kl_args_tea>(args), vb);
+      break;
+    case KL_T_SAD:
+      if constexpr (TC) sad_block(load_args<kl_args_sad>(args), vb);
+      break;
+    case KL_T_STENCIL:
+      if constexpr (TC) stencil_block(load_args<kl_args_stencil>(args), vb);
+      break;
+    case KL_T_MRIQ:
+      if constexpr (TC) mriq_block(load_args<kl_args_mriq>(args), st.s, vb, smem);
       break;
     default: break;
   }

@@ -21,10 +21,11 @@ KL_OK, KL_EINVAL, KL_ENOMEM, KL_EAGAIN, KL_ETIMEDOUT, KL_ECUDA, KL_EDEVICE_TIMEO
 KL_PENDING, KL_RUNNING, KL_DONE, KL_ERROR = 0, 1, 2, 3
 
 (KL_T_GATHER, KL_T_BLACKSCHOLES, KL_T_GEMM_F32, KL_T_SPMV_CSR, KL_T_PCHASE, KL_T_TRIAD,
- KL_T_HIST256, KL_T_ESCAPE, KL_T_BITONIC, KL_T_MATADD, KL_T_GEMM_BF16) = range(11)
-KL_T_COUNT = 11
+ KL_T_HIST256, KL_T_ESCAPE, KL_T_BITONIC, KL_T_MATADD, KL_T_GEMM_BF16, KL_T_TEA, KL_T_SAD, KL_T_STENCIL,
+ KL_T_MRIQ) = range(15)
+KL_T_COUNT = 15
 TYPE_NAMES = ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256",
-              "escape", "bitonic", "matadd", "gemm_bf16"]
+              "escape", "bitonic", "matadd", "gemm_bf16", "tea", "sad", "stencil", "mriq"]
 KL_RATIO_BALANCED, KL_RATIO_MAX_CP, KL_RATIO_FIXED = 0, 1, 2
 KL_BASE_SERIAL, KL_BASE_MULTISTREAM, KL_SERVE_COSCHED = 0, 1, 2
 KL_CFG_BACKFILL = 1
@@ -85,9 +86,28 @@ class kl_args_gemm_bf16(C.Structure):
     _fields_ = [("A", P), ("Bt", P), ("C", P), ("tmaps", P), ("M", U32), ("N", U32), ("K", U32), ("pad", U32)]
 
 
+class kl_args_tea(C.Structure):
+    _fields_ = [("in_", P), ("out", P), ("key", U32 * 4), ("n", U64)]
+
+
+class kl_args_sad(C.Structure):
+    _fields_ = [("cur", P), ("ref", P), ("sad", P), ("width", U32), ("height", U32), ("range", U32),
+                ("pad", U32)]
+
+
+class kl_args_stencil(C.Structure):
+    _fields_ = [("in_", P), ("out", P), ("nx", U32), ("ny", U32), ("nz", U32), ("pad", U32),
+                ("c0", F32), ("c1", F32)]
+
+
+class kl_args_mriq(C.Structure):
+    _fields_ = [("kx", P), ("ky", P), ("kz", P), ("phiR", P), ("phiI", P), ("phiMag", P), ("x", P), ("y", P),
+                ("z", P), ("Qr", P), ("Qi", P), ("numK", U32), ("numX", U32)]
+
+
 ARGS_TYPES = [kl_args_gather, kl_args_blackscholes, kl_args_gemm_f32, kl_args_spmv_csr,
               kl_args_pchase, kl_args_triad, kl_args_hist256, kl_args_escape, kl_args_bitonic,
-              kl_args_matadd, kl_args_gemm_bf16]
+              kl_args_matadd, kl_args_gemm_bf16, kl_args_tea, kl_args_sad, kl_args_stencil, kl_args_mriq]
 
 
 class kl_tenant_shape(C.Structure):

@@ -34,7 +34,7 @@ def scaled_sizes(name, scale):
     if name == "gemm_bf16":
         m = max(128, int(4096 * scale ** (1 / 3)) // 128 * 128)
         return dict(M=m, N=m, K=m)
-    if name in ("gather", "matadd"):
+    if name in ("gather", "matadd", "tea", "sad", "stencil", "mriq"):
         return s
     if name == "gemm_f32":
         m = max(64, int(1024 * scale ** (1 / 3)) // 64 * 64)
@@ -60,7 +60,7 @@ METRICS = ",".join([
 
 TYPE_OF_KERNEL = {f"native_kernel<{i}>": n for i, n in enumerate(
     ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256", "escape", "bitonic",
-     "matadd", "gemm_bf16"])}
+     "matadd", "gemm_bf16", "tea", "sad", "stencil", "mriq"])}
 
 # Types left out of the a0/b0 fit, with the reason (their errors are still
 # reported): the Markov model's warps are either ready or waiting on memory.

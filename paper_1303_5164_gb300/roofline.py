@@ -37,6 +37,15 @@ def algo_bytes(name: str, inp: dict) -> int:
         return 12 * inp["n"] * inp["n"]
     if name == "gemm_bf16":
         return 2 * (inp["M"] * inp["K"] + inp["N"] * inp["K"]) + 4 * inp["M"] * inp["N"]
+    if name == "tea":
+        return 16 * inp["n"]                      # 8 bytes in, 8 out per 64-bit block
+    if name == "sad":
+        D = 2 * inp["range"] + 1
+        return 2 * inp["width"] * inp["height"] + 4 * (inp["width"] // 4) * (inp["height"] // 4) * D * D
+    if name == "stencil":
+        return 8 * inp["nx"] * inp["ny"] * inp["nz"]  # neighbours come from cache
+    if name == "mriq":
+        return 24 * inp["numK"] + 20 * inp["numX"]
     raise ValueError(name)
 
 
@@ -61,6 +70,11 @@ def fp32_flops(name: str, inp: dict, escape_iters: int | None = None) -> int:
         return ESCAPE_FLOPS_PER_ITER * int(escape_iters or 0)
     if name == "matadd":
         return inp["n"] * inp["n"]
+    if name == "stencil":
+        return 8 * inp["nx"] * inp["ny"] * inp["nz"]
+    if name == "mriq":
+        # per (point, sample): dot product 5, angle 1, reduction 4, polynomials 16, accumulation 4
+        return 30 * inp["numK"] * inp["numX"]
     return 0
 
 

@@ -53,7 +53,7 @@ class Tenant:
         out = {}
         for k in self.outputs:
             a = self.bufs[k].cpu().numpy()
-            if k in ("hist", "count", "out") and self.name in ("hist256", "escape", "bitonic"):
+            if k in ("hist", "count", "out", "sad") and self.name in ("hist256", "escape", "bitonic", "tea", "sad"):
                 a = a.view(np.uint32)
             out[k] = a
         return out
@@ -139,6 +139,34 @@ def make(name: str, inp: dict, device="cuda") -> Tenant:
         b["tmaps"] = torch.frombuffer(bytearray(bytes(maps)), dtype=torch.uint8).to(device)
         args.tmaps = _ptr(b["tmaps"])
         outs = ["C"]
+    elif name == "tea":
+        b["in_"] = _dev(inp["words"], device)
+        b["out"] = _empty(2 * inp["n"], torch.int32, device)
+        args = K.kl_args_tea(_ptr(b["in_"]), _ptr(b["out"]), (K.U32 * 4)(*[int(k) for k in inp["key"]]), inp["n"])
+        outs = ["out"]
+    elif name == "sad":
+        b["cur"] = torch.from_numpy(np.ascontiguousarray(inp["cur"])).to(device)
+        b["ref"] = torch.from_numpy(np.ascontiguousarray(inp["ref"])).to(device)
+        D = 2 * inp["range"] + 1
+        b["sad"] = _empty((inp["width"] // 4) * (inp["height"] // 4) * D * D, torch.int32, device)
+        args = K.kl_args_sad(_ptr(b["cur"]), _ptr(b["ref"]), _ptr(b["sad"]), inp["width"], inp["height"],
+                             inp["range"], 0)
+        outs = ["sad"]
+    elif name == "stencil":
+        b["in_"] = _dev(inp["grid"], device)
+        b["out"] = _empty(inp["nx"] * inp["ny"] * inp["nz"], torch.float32, device)
+        args = K.kl_args_stencil(_ptr(b["in_"]), _ptr(b["out"]), inp["nx"], inp["ny"], inp["nz"], 0,
+                                 float(inp["c0"]), float(inp["c1"]))
+        outs = ["out"]
+    elif name == "mriq":
+        for k in ("kx", "ky", "kz", "phiR", "phiI", "x", "y", "z"):
+            b[k] = _dev(inp[k], device)
+        b["phiMag"] = _empty(inp["numK"], torch.float32, device)
+        b["Qr"] = _empty(inp["numX"], torch.float32, device)
+        b["Qi"] = _empty(inp["numX"], torch.float32, device)
+        args = K.kl_args_mriq(*[_ptr(b[k]) for k in ("kx", "ky", "kz", "phiR", "phiI", "phiMag", "x", "y", "z",
+                                                     "Qr", "Qi")], inp["numK"], inp["numX"])
+        outs = ["phiMag", "Qr", "Qi"]
     elif name == "matadd":
         b["a"], b["b"] = _dev(inp["a"], device), _dev(inp["b"], device)
         b["c"] = _empty((inp["n"], inp["n"]), torch.float32, device)
@@ -165,5 +193,9 @@ SIZES_MIX = {
 MIX_TYPES = ["gemm_f32", "spmv_csr", "blackscholes", "pchase", "triad", "hist256", "escape", "bitonic"]
 # the other types at the sizes they are profiled and validated at: the
 # two-tenant pair's gather, the MatrixAdd example, the 4096^3 tensor-core GEMM
-SIZES_OTHER = {"gather": dict(n=1 << 20), "matadd": dict(n=256), "gemm_bf16": dict(M=4096, N=4096, K=4096)}
+SIZES_OTHER = {"gather": dict(n=1 << 20), "matadd": dict(n=256), "gemm_bf16": dict(M=4096, N=4096, K=4096),
+               # the paper's remaining benchmark kernels, at its input sizes (Table tb:description)
+               "tea": dict(n=20971520), "sad": dict(width=1920, height=1072, range=8),
+               "stencil": dict(nx=256, ny=256, nz=256),  # the paper's grid is 512^3; 256^3 keeps captures small
+               "mriq": dict(numK=512, numX=2097152)}
 SIZES_ALL = {**SIZES_MIX, **SIZES_OTHER}

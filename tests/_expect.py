@@ -37,6 +37,15 @@ def expected(name: str, inp: dict) -> dict:
     if name == "gemm_bf16":
         c64, cabs = OT.gemm_bf16(inp["A"], inp["Bt"])
         return {"_C64": c64, "_Cabs": cabs}
+    if name == "tea":
+        return {"out": OT.tea(inp["words"], inp["key"], inp["n"])}
+    if name == "sad":
+        return {"sad": OT.sad(inp["cur"], inp["ref"], inp["width"], inp["height"], inp["range"])}
+    if name == "stencil":
+        return {"out": OT.stencil7(inp["grid"], inp["nx"], inp["ny"], inp["nz"], inp["c0"], inp["c1"])}
+    if name == "mriq":
+        pm, qr, qi = OT.mriq(inp)
+        return {"phiMag": pm, "Qr": qr, "Qi": qi}
     raise ValueError(name)
 
 

@@ -24,6 +24,10 @@ CASES = {
     "matadd": dict(n=256),
     # 2 x 3 tiles of 128 x 64 with ragged M and N, 3 K-slices of 64 with a ragged 8
     "gemm_bf16": dict(M=200, N=132, K=136),
+    "tea": dict(n=3 * 512 + 7),                                 # odd leftover block
+    "sad": dict(width=64, height=36, range=3),                  # 7056 values: 28 blocks, ragged
+    "stencil": dict(nx=300, ny=17, nz=9),                       # rows of 2 blocks, the second ragged
+    "mriq": dict(numK=300, numX=1000),                          # two sample chunks, ragged point block
 }
 
 

@@ -277,3 +277,103 @@ def test_gemm_bf16_matches_fp32_chain_within_its_bound(oracle_tenants):
     ii = np.array([0, 5, 32, 17]); jj = np.array([0, 19, 3, 11])
     cs, ss = OT.gemm_bf16_sample(inp["A"], inp["Bt"], ii, jj)
     assert np.allclose(cs, c64[ii, jj], rtol=0, atol=1e-12) and np.allclose(ss, s[ii, jj], rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- TEA, SAD, stencil, MRI-Q
+
+def test_tea_known_answer_and_inverse(oracle_tenants):
+    OT = oracle_tenants
+    # the cipher's published test vector: zero key, zero block
+    assert OT.tea(np.zeros(2, np.uint32), np.zeros(4, np.uint32), 1).tolist() == [0x41EA3A0A, 0x94BAA940]
+    inp = gen.gen_tea(4, 0, 257)
+    ct = OT.tea(inp["words"], inp["key"], inp["n"])
+    # decryption runs the cycles backwards (sum from 32 * delta down); it must
+    # give back every plaintext block
+    k = [int(x) for x in inp["key"]]
+    v0 = ct[0::2].astype(np.uint64)
+    v1 = ct[1::2].astype(np.uint64)
+    M = np.uint64(0xFFFFFFFF)
+    s = np.uint64((0x9E3779B9 * 32) & 0xFFFFFFFF)
+    for _ in range(32):
+        v1 = (v1 - ((((v0 << np.uint64(4)) & M) + np.uint64(k[2])) ^ ((v0 + s) & M) ^ ((v0 >> np.uint64(5)) + np.uint64(k[3])))) & M
+        v0 = (v0 - ((((v1 << np.uint64(4)) & M) + np.uint64(k[0])) ^ ((v1 + s) & M) ^ ((v1 >> np.uint64(5)) + np.uint64(k[1])))) & M
+        s = (s + np.uint64((1 << 32) - 0x9E3779B9)) & M  # s - delta modulo 2^32
+    assert np.array_equal(v0.astype(np.uint32), inp["words"][0::2])
+    assert np.array_equal(v1.astype(np.uint32), inp["words"][1::2])
+
+
+def test_sad_shifted_frame_and_brute_force(oracle_tenants):
+    OT = oracle_tenants
+    W, H, R = 40, 24, 3
+    cur = (np.arange(W * H, dtype=np.uint64) * np.uint64(2654435761) >> np.uint64(13)).astype(np.uint8).reshape(H, W)
+    dx, dy = 2, -1
+    ref = np.roll(cur, (dy, dx), axis=(0, 1))
+    sad = OT.sad(cur, ref, W, H, R).reshape(H // 4, W // 4, 2 * R + 1, 2 * R + 1)
+    # interior blocks (no wrap, no clamping) match exactly at the true motion
+    for by in range(1, H // 4 - 1):
+        for bx in range(1, W // 4 - 1):
+            assert sad[by, bx, dy + R, dx + R] == 0
+            assert sad[by, bx].min() == 0
+    # identical frames: zero at displacement 0 everywhere
+    assert np.all(OT.sad(cur, cur, W, H, R).reshape(-1, (2 * R + 1) ** 2)[:, R * (2 * R + 1) + R] == 0)
+    # brute force with numpy clipping on a few (block, displacement) pairs
+    rng = np.random.default_rng(0)
+    full = OT.sad(cur, ref, W, H, R)
+    for _ in range(50):
+        by, bx = rng.integers(0, H // 4), rng.integers(0, W // 4)
+        ddy, ddx = rng.integers(-R, R + 1), rng.integers(-R, R + 1)
+        ys = np.clip(np.arange(4 * by, 4 * by + 4) + ddy, 0, H - 1)
+        xs = np.clip(np.arange(4 * bx, 4 * bx + 4) + ddx, 0, W - 1)
+        want = np.abs(cur[4 * by:4 * by + 4, 4 * bx:4 * bx + 4].astype(int) - ref[np.ix_(ys, xs)].astype(int)).sum()
+        o = ((by * (W // 4) + bx) * (2 * R + 1) + ddy + R) * (2 * R + 1) + ddx + R
+        assert full[o] == want
+
+
+def test_stencil_closed_forms(oracle_tenants):
+    OT = oracle_tenants
+    nx, ny, nz = 9, 7, 5
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    inner = (x > 0) & (y > 0) & (z > 0) & (x < nx - 1) & (y < ny - 1) & (z < nz - 1)
+    const = np.full((nz, ny, nx), 1.5, np.float32)
+    out = OT.stencil7(const, nx, ny, nz, 0.25, 0.125).reshape(nz, ny, nx)
+    assert np.all(out[inner] == np.float32(1.5 * (0.25 + 6 * 0.125)))
+    assert np.all(out[~inner] == 1.5)                           # faces are copied
+    lin = (3 * x - 2 * y + 5 * z).astype(np.float32)            # discrete Laplacian of a linear field is 0
+    out = OT.stencil7(lin, nx, ny, nz, -6.0, 1.0).reshape(nz, ny, nx)
+    assert np.all(out[inner] == 0.0)
+    quad = (x * x).astype(np.float32)                           # ... of x^2 is 2
+    out = OT.stencil7(quad, nx, ny, nz, -6.0, 1.0).reshape(nz, ny, nx)
+    assert np.all(out[inner] == 2.0)
+
+
+def test_sincosf_against_binary64(oracle_tenants):
+    OT = oracle_tenants
+    xs = np.linspace(-80.0, 80.0, 20001).astype(np.float32)
+    for a in xs[::7]:
+        s, c = OT.sincosf(float(a))
+        a64 = float(a)
+        # a few units of 2^-24 of the result's scale: the reduction's error
+        # grows with the quadrant number |n| <= 51 here
+        tol = 6e-8 * (4 + abs(a64) / 8)
+        assert abs(s - np.sin(a64)) <= tol and abs(c - np.cos(a64)) <= tol, (a, s, c)
+    assert OT.sincosf(0.0) == (0.0, 1.0)
+
+
+def test_mriq_against_binary64(oracle_tenants):
+    OT = oracle_tenants
+    inp = gen.gen_mriq(5, 1, 96, 40)
+    pm, qr, qi = OT.mriq(inp)
+    k = {n: inp[n].astype(np.float64) for n in ("kx", "ky", "kz", "phiR", "phiI", "x", "y", "z")}
+    pm64 = k["phiR"] ** 2 + k["phiI"] ** 2
+    assert np.all(np.abs(pm - pm64) <= 2 * 2.0 ** -24 * pm64)
+    t = np.outer(k["x"], k["kx"]) + np.outer(k["y"], k["ky"]) + np.outer(k["z"], k["kz"])
+    ang = 2 * np.pi * t
+    qr64 = (np.cos(ang) * pm64).sum(axis=1)
+    qi64 = (np.sin(ang) * pm64).sum(axis=1)
+    # per term: angle error ~ 6 u |2 pi t|-scale plus the sine/cosine's own few
+    # u; the sum of numK binary32 terms adds numK u sum(pm)
+    u = 2.0 ** -24
+    scale = np.abs(np.outer(k["x"], k["kx"])) + np.abs(np.outer(k["y"], k["ky"])) + np.abs(np.outer(k["z"], k["kz"]))
+    bound = (pm64 * (6 * u * 2 * np.pi * scale + 8 * u + 6e-8 * (4 + np.abs(ang) / 8))).sum(axis=1) \
+        + inp["numK"] * u * pm64.sum()
+    assert np.all(np.abs(qr - qr64) <= bound) and np.all(np.abs(qi - qi64) <= bound)

@@ -137,6 +137,46 @@ def gen_gemm_bf16(cs: int, ti: int, M: int, N: int, K: int) -> dict:
     return dict(A=A, Bt=Bt, M=M, N=N, K=K)
 
 
+def _u32(seed: int, n: int) -> np.ndarray:
+    return (splitmix64(seed, n) >> np.uint64(32)).astype(np.uint32)
+
+
+def gen_tea(cs: int, ti: int, n: int) -> dict:
+    """n 64-bit plaintext blocks (2n uint32 words) and a 128-bit key."""
+    return dict(words=_u32(stream_seed(cs, ti, "words"), 2 * n), key=_u32(stream_seed(cs, ti, "key"), 4), n=n)
+
+
+def gen_sad(cs: int, ti: int, width: int = 1920, height: int = 1072, range: int = 8) -> dict:
+    """Two 8-bit frames: random luma, and the same frame moved by one global
+    motion vector within the search range plus small noise (so every block has
+    a clear SAD minimum, as between consecutive video frames)."""
+    cur = (_u32(stream_seed(cs, ti, "cur"), width * height) >> np.uint32(24)).astype(np.uint8).reshape(height, width)
+    mv = _u32(stream_seed(cs, ti, "mv"), 2) % np.uint32(2 * range + 1)
+    dx, dy = int(mv[0]) - range, int(mv[1]) - range
+    noise = (_u32(stream_seed(cs, ti, "noise"), width * height) >> np.uint32(29)).astype(np.int16).reshape(height, width)
+    ref = np.clip(np.roll(cur, (dy, dx), axis=(0, 1)).astype(np.int16) + noise - 3, 0, 255).astype(np.uint8)
+    return dict(cur=cur, ref=ref, width=width, height=height, range=range, mv=(dx, dy))
+
+
+def gen_stencil(cs: int, ti: int, nx: int, ny: int, nz: int, c0: float = 0.25, c1: float = 0.125) -> dict:
+    """A binary32 grid of N(0,1) values and the stencil's two coefficients."""
+    return dict(grid=normal_f32(stream_seed(cs, ti, "grid"), nx * ny * nz).reshape(nz, ny, nx),
+                nx=nx, ny=ny, nz=nz, c0=c0, c1=c1)
+
+
+def gen_mriq(cs: int, ti: int, numK: int, numX: int) -> dict:
+    """k-space samples (coordinates U[-1/2, 1/2), phi ~ N(0,1)) and image
+    points with coordinates U[-8, 8)."""
+    return dict(kx=_uniform_f32(stream_seed(cs, ti, "kx"), numK, -0.5, 0.5),
+                ky=_uniform_f32(stream_seed(cs, ti, "ky"), numK, -0.5, 0.5),
+                kz=_uniform_f32(stream_seed(cs, ti, "kz"), numK, -0.5, 0.5),
+                phiR=normal_f32(stream_seed(cs, ti, "phiR"), numK),
+                phiI=normal_f32(stream_seed(cs, ti, "phiI"), numK),
+                x=_uniform_f32(stream_seed(cs, ti, "x"), numX, -8.0, 8.0),
+                y=_uniform_f32(stream_seed(cs, ti, "y"), numX, -8.0, 8.0),
+                z=_uniform_f32(stream_seed(cs, ti, "z"), numX, -8.0, 8.0), numK=numK, numX=numX)
+
+
 def spmv_xm_for_mean(mean: float = 16.0, alpha: float = 2.5, dmax: int = 8192) -> float:
     """Lower bound x_m of a Pareto(pdf ~ x^-alpha) truncated at dmax+1 such
     that E[floor(X)] = mean (bisection on the closed-form expectation)."""
@@ -237,5 +277,6 @@ def gen_tenant(name: str, cs: int, ti: int, **size) -> dict:
     fn = {"gather": gen_gather, "blackscholes": gen_blackscholes,
           "gemm_f32": gen_gemm_f32, "spmv_csr": gen_spmv_csr, "pchase": gen_pchase,
           "triad": gen_triad, "hist256": gen_hist256, "escape": gen_escape,
-          "bitonic": gen_bitonic, "matadd": gen_matadd, "gemm_bf16": gen_gemm_bf16}[name]
+          "bitonic": gen_bitonic, "matadd": gen_matadd, "gemm_bf16": gen_gemm_bf16, "tea": gen_tea,
+          "sad": gen_sad, "stencil": gen_stencil, "mriq": gen_mriq}[name]
     return fn(cs, ti, **size)
