@@ -56,7 +56,8 @@ METRICS = ",".join([
     "smsp__inst_executed_op_global_ld.sum", "smsp__inst_executed_op_ldgsts.sum",
     "l1tex__t_requests_pipe_lsu_mem_global_op_ld.sum", "l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum",
     "sm__inst_executed.avg.per_cycle_active", "sm__warps_active.avg.per_cycle_active",
-    "dram__bytes_read.sum", "dram__bytes_write.sum", "launch__grid_size"])
+    "dram__bytes_read.sum", "dram__bytes_write.sum", "launch__grid_size",
+    "l1tex__t_sector_pipe_lsu_mem_global_op_ld_hit_rate.pct"])
 
 TYPE_OF_KERNEL = {f"native_kernel<{i}>": n for i, n in enumerate(
     ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256", "escape", "bitonic",
@@ -157,10 +158,14 @@ def ingest(csv_path, latency_json, out_path, hbm_gbs=None, n_sm=None):
         key = next((v for k, v in TYPE_OF_KERNEL.items() if k in kname.replace(" ", "")), None)
         if key is None:
             continue
-        a = agg.setdefault(key, {"inst": 0, "ld": 0, "req": 0, "sec": 0, "dur_ns": 0, "cyc": 0,
+        a = agg.setdefault(key, {"inst": 0, "ld": 0, "ld_miss": 0, "req": 0, "sec": 0, "dur_ns": 0, "cyc": 0,
                                  "dram": 0, "blocks": 0, "warps_x_cyc": 0, "launches": 0})
         a["inst"] += _num(r["smsp__inst_executed.sum"])
-        a["ld"] += _num(r["smsp__inst_executed_op_global_ld.sum"]) + _num(r["smsp__inst_executed_op_ldgsts.sum"])
+        ld = _num(r["smsp__inst_executed_op_global_ld.sum"]) + _num(r["smsp__inst_executed_op_ldgsts.sum"])
+        a["ld"] += ld
+        # loads that miss L1 (the ones that wait an L2 or DRAM latency)
+        hit = r.get("l1tex__t_sector_pipe_lsu_mem_global_op_ld_hit_rate.pct")
+        a["ld_miss"] += ld * (1.0 - min(100.0, max(0.0, _num(hit))) / 100.0) if hit not in (None, "", "n/a") else ld
         a["req"] += _num(r["l1tex__t_requests_pipe_lsu_mem_global_op_ld.sum"])
         a["sec"] += _num(r["l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum"])
         dur = _num(r["gpu__time_duration.sum"])
@@ -185,7 +190,8 @@ def ingest(csv_path, latency_json, out_path, hbm_gbs=None, n_sm=None):
         ipc_meas = a["inst"] / (a["cyc"] * nsm) if a["cyc"] else 0.0
         w_sm = a["warps_x_cyc"] / a["cyc"] if a["cyc"] else 8.0
         types[name] = dict(
-            R_m=a["ld"] / a["inst"], f_u=fu, m_c=4.0, m_u=32.0, L0=L0_ns * 1e-9 * f,
+            R_m=a["ld_miss"] / a["inst"], R_m_all_loads=a["ld"] / a["inst"], f_u=fu, m_c=4.0, m_u=32.0,
+            L0=L0_ns * 1e-9 * f,
             I_block=a["inst"] / a["blocks"], PUR=a["inst"] / (a["cyc"] * nsm * 4.0),
             MUR=a["dram"] / (a["dur_ns"] * 1e-9 * hbm), warps_per_block=8,
             ipc_measured=ipc_meas, warps_per_sm=w_sm, sectors_per_request=m, launches=a["launches"],
@@ -221,6 +227,13 @@ def ingest(csv_path, latency_json, out_path, hbm_gbs=None, n_sm=None):
            "ipc_mae_per_sm": mae, "ipc_mae_types": fit,
            "fit_excluded": {n: FIT_EXCLUDE[n] for n in types if n in FIT_EXCLUDE},
            "ipc_peak_per_sm": 4.0, "latency": lat, "types": types}
+    if os.path.exists(out_path):
+        # slice sizes come from the autotuner, not from the counters: keep them
+        with open(out_path) as fh:
+            prev = json.load(fh)
+        for k in ("slices", "slice_autotune"):
+            if k in prev:
+                out[k] = prev[k]
     with open(out_path, "w") as fh:
         json.dump(out, fh, indent=1, sort_keys=True)
     print(json.dumps({"a0": a0, "b0": b0, "ipc_mae_per_sm": mae,
