@@ -261,9 +261,10 @@ typedef enum {
                                types after it; without it a serving run refuses
                                those types (KL_EINVAL). Batch runs pick the build
                                from the kernels they hold. */
-#define KL_CFG_WIDE_FILL 16u /* backfill considers 8 pending kernels per phase
-                               (both chain-lane kernels, then the lowest pending
-                               ones) instead of 4; default on */
+#define KL_CFG_WIDE_FILL 16u /* backfill considers two pending kernels per slot
+                               of an SM (8 at 4 slots, 16 at 8; both chain-lane
+                               kernels, then the lowest pending ones) instead
+                               of 4; default on */
 #define KL_CFG_LAZY_ARRIVAL 32u /* serving: an arrival re-plans only when no pair is
                                running (idle or solo phase); otherwise the new
                                kernel waits in R for the next re-plan, which
@@ -273,6 +274,13 @@ typedef enum {
                                split uniformly at random (counter-based SplitMix64
                                of kl_config.plan_seed and the phase number)
                                instead of the largest-CP pair */
+#define KL_CFG_LIGHT_BUILD 128u /* a batch run whose kernels are all of the light
+                               types (gather, Black-Scholes, SpMV, triad,
+                               escape-time, MatrixAdd, TEA, stencil: short
+                               bodies within 32 registers) uses the co-scheduler
+                               build with 8 CTAs per SM instead of 4, and the CP
+                               table for 8 slots; needs slots_per_sm = 0 and no
+                               kl_set_cp_table override; default on */
 #define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their
@@ -282,7 +290,8 @@ typedef enum {
 
 typedef struct {
     int32_t device;                 /* CUDA ordinal (default 0)                     */
-    uint32_t slots_per_sm;          /* co-scheduler CTAs per SM; 0 = occupancy limit */
+    uint32_t slots_per_sm;          /* co-scheduler CTAs per SM; 0 = occupancy limit
+                                       of the build a run uses                      */
     uint32_t max_tenants;           /* pending-set capacity per run (default 4096)  */
     uint32_t model_states;          /* 2 or 3 (uncoalesced extension); default 3    */
     uint32_t ratio_policy;          /* kl_ratio_policy                              */

@@ -30,13 +30,16 @@ def tune(types, p=0.02, reps=3, seed=6):
     from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
     build.build()
     rt = K.Runtime()
-    S = rt.run_stats().slots_per_sm
     n_sm = rt.model_params().n_sm
-    out = {"p": p, "slots_per_sm": S, "n_sm": n_sm, "slices": {}, "times_us": {}, "overhead": {}}
+    out = {"p": p, "n_sm": n_sm, "slices": {}, "times_us": {}, "overhead": {}, "slots_per_sm": {}}
     for i, ty in enumerate(types):
-        inp = gen.gen_tenant(ty, seed, i, **T.SIZES_MIX[ty])
+        inp = gen.gen_tenant(ty, seed, i, **T.SIZES_ALL[ty])
         t = T.make(ty, inp)
         sh = t.shape()
+        rt.submit(t.type, t.args)  # slots per SM of the build this type runs in
+        rt.launch()
+        assert rt.drain() == 0
+        S = rt.run_stats().slots_per_sm
         stage_blocks = int(sh.grid[0]) if ty != "hist256" else int(sh.total_blocks - 1)
         ref = max(1, math.ceil(stage_blocks / (n_sm * S)))
         cands = sorted({c for c in (1, 2, 4, 8, 16, 32, 64) if c <= stage_blocks} | {ref})
@@ -56,6 +59,7 @@ def tune(types, p=0.02, reps=3, seed=6):
         out["slices"][ty] = chosen
         out["times_us"][ty] = {str(c): round(v, 2) for c, v in times.items()}
         out["overhead"][ty] = round(times[chosen] / tns - 1.0, 4)
+        out["slots_per_sm"][ty] = S
         print(ty, "ref", ref, "chosen", chosen, out["times_us"][ty], flush=True)
         del t
         torch.cuda.empty_cache()
@@ -67,7 +71,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--p", type=float, default=0.02)
-    ap.add_argument("--types", default="gemm_f32,spmv_csr,blackscholes,pchase,triad,hist256,escape,bitonic")
+    ap.add_argument("--types", default="gemm_f32,spmv_csr,blackscholes,pchase,triad,hist256,escape,bitonic,gather,"
+                                       "tea,sad,stencil,mriq")
     a = ap.parse_args(argv)
     res = tune(a.types.split(","), a.p)
     with open(a.out, "w") as f:

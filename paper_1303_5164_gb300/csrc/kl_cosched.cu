@@ -24,6 +24,7 @@
 // after which the run records KL_EDEVICE_TIMEOUT (or, when serving and idle,
 // ends the run) and every CTA returns.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "kl_internal.h"
@@ -81,8 +82,11 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
   return x ^ (x >> 31);
 }
 
-// Co-resident CTAs per SM: 4 x 256 threads at up to 64 registers each.
+// Co-resident CTAs per SM: 4 x 256 threads at up to 64 registers each (plain
+// and full builds), 8 x 256 at up to 32 registers (light build).
 constexpr int kCtasPerSm = 4;
+constexpr int kCtasPerSmLight = 8;
+constexpr int ctas_per_sm(int build) { return build == tn::kBuildLight ? kCtasPerSmLight : kCtasPerSm; }
 
 enum : uint32_t { kActRun = 0, kActWait = 1, kActExit = 2, kActReplan = 3, kActIntake = 4 };
 enum : int { kPulled = 0, kBlocked = 1, kExhausted = 2 };
@@ -96,6 +100,12 @@ struct CtaCtl {
   int32_t wait_failed;
   uint32_t from, to;   // dispatcher: kernels to copy in
   uint32_t mine;       // dispatcher: this CTA claimed the re-plan
+  uint32_t own;        // the slice came from this slot's own kernel in the current phase
+  uint32_t own_seq;    // ... the phase that gave the slot that kernel
+  int32_t pf_tenant;   // a slice claimed ahead while the previous one ran (-1: none)
+  uint32_t pf_g0, pf_g1;
+  uint32_t pf_more;    // the phase was still own_seq when that slice was claimed
+  int32_t args_of;     // kernel whose arguments s_args holds (-1: none)
   unsigned long long acc_wait, acc_stage, acc_plan;  // this CTA's time accounting (thread 0)
 };
 
@@ -126,7 +136,6 @@ __device__ __forceinline__ tn::Stage stage_at(const TenantDev& d, uint32_t type,
   return g < b0 ? tn::Stage{0u, 0u, b0} : tn::Stage{1u, b0, total};
 }
 
-template <bool TC>
 __device__ __forceinline__ int try_pull(TenantDev* T, const RunDev* R, int32_t t, uint32_t rank, uint32_t n_sm,
                                         uint32_t& g0, uint32_t& g1) {
   TenantDev& d = tenant(T, R, (uint32_t)t);
@@ -158,7 +167,7 @@ struct ScanPart {
   int32_t first;
   unsigned long long pmask;
   uint32_t nlow, nms;
-  int32_t lowp[10];
+  int32_t lowp[kFill + 2];
   int32_t lowms[4];
   int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
 };
@@ -192,7 +201,7 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
     for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
     uint32_t npend = 0, nlow = 0, nms = 0;
     unsigned long long pmask = 0ull;
-    int32_t lowp[10], lowms[4];
+    int32_t lowp[kFill + 2], lowms[4];
     int32_t first_pending = -1;
     const uint32_t nchunk = hi > lo ? (hi - lo + 31u) / 32u : 0u;
     const uint32_t cpw = (nchunk + kWarps - 1) / kWarps;
@@ -213,7 +222,7 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
       npend += __popc(pb);
       if (pb && first_pending < 0) first_pending = (int32_t)(base + __ffs(pb) - 1);
       if (base < 64) pmask |= (unsigned long long)pb << base;
-      for (uint32_t m = pb; m && nlow < 10; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
+      for (uint32_t m = pb; m && nlow < (uint32_t)kFill + 2u; m &= m - 1) lowp[nlow++] = (int32_t)(base + __ffs(m) - 1);
       const uint32_t msb = __ballot_sync(0xffffffffu, pend && multi);
       for (uint32_t m = msb; m && nms < 4; m &= m - 1) lowms[nms++] = (int32_t)(base + __ffs(m) - 1);
 #pragma unroll
@@ -249,14 +258,14 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
   for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
   uint32_t npend = 0, nlow = 0, nms = 0;
   unsigned long long pmask = 0ull;
-  int32_t lowp[10], lowms[4];
+  int32_t lowp[kFill + 2], lowms[4];
   int32_t first_pending = -1;
   for (int w = 0; w < kWarps; ++w) {
     const ScanPart& q = parts[w];
     npend += q.npend;
     pmask |= q.pmask;
     if (first_pending < 0) first_pending = q.first;
-    for (uint32_t f = 0; f < q.nlow && nlow < 10; ++f) lowp[nlow++] = q.lowp[f];
+    for (uint32_t f = 0; f < q.nlow && nlow < (uint32_t)kFill + 2u; ++f) lowp[nlow++] = q.lowp[f];
     for (uint32_t f = 0; f < q.nms && nms < 4; ++f) lowms[nms++] = q.lowms[f];
     for (int t = 0; t < KL_T_COUNT; ++t) {
       const int32_t c[2] = {q.low1[t], q.low2[t]};
@@ -382,7 +391,9 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
   // barriers overlap other work instead of forming the tail of the run), then
   // the lowest pending sequence numbers
   for (int f = 0; f < kFill; ++f) ph.fill[f] = -1;
-  const uint32_t nfill = (R->flags & KL_CFG_WIDE_FILL) ? (uint32_t)kFill : 4u;
+  // two candidates per slot of an SM (8 at 4 slots, 16 at 8): kernels with
+  // fewer blocks than the GPU has slots still fill it
+  const uint32_t nfill = (R->flags & KL_CFG_WIDE_FILL) ? min((uint32_t)kFill, 2u * R->slots) : 4u;
   uint32_t c = 0;
   if (ph.A >= 0 && (R->flags & KL_CFG_FILL_TYPES)) {
     const uint32_t ta = tenant(T, R, ph.A).type;
@@ -538,15 +549,17 @@ __device__ void dispatcher(TenantDev* T, RunDev* R, PhaseDev* P, CtaCtl& ctl, ch
   }
 }
 
-// TC = true: the build that can run the tensor-core BF16 GEMM tenant (used
-// only for runs that contain one; see run_block).
-template <bool TC>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev* __restrict__ T, RunDev* __restrict__ R,
+// BUILD: tn::kBuildPlain, kBuildFull (the only one that can run the
+// tensor-core BF16 GEMM tenant) or kBuildLight; the host picks the smallest
+// build that holds every type of the run (see tn::run_block).
+template <int BUILD>
+__global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(TenantDev* __restrict__ T, RunDev* __restrict__ R,
                                                                       PhaseDev* __restrict__ P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ CtaCtl ctl;
   __shared__ uint32_t s_slot;
   __shared__ uint32_t s_tmem;  // TMEM columns of this CTA (BF16 GEMM blocks)
+  __shared__ __align__(16) unsigned char s_args[KL_MAX_ARGS_BYTES];  // arguments of the running slice
   const int tid = threadIdx.x;
   if (tid == 0) {
     const uint32_t sm = smid() & (kMaxSM - 1);
@@ -556,10 +569,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
   }
   __syncthreads();
   const tn::BlockCtx tcx{&s_tmem, &R->error, R->wait_limit_ns};
-  if constexpr (TC) tn::acquire_tmem(tcx);
+  if constexpr (BUILD == tn::kBuildFull) tn::acquire_tmem(tcx);
   if (R->serve && blockIdx.x == 0) {
     dispatcher(T, R, P, ctl, smem);
-    if constexpr (TC) tn::release_tmem(tcx);
+    if constexpr (BUILD == tn::kBuildFull) tn::release_tmem(tcx);
     if (tid == 0) atomicAdd(&R->ctas_done, 1u);
     return;
   }
@@ -569,15 +582,29 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
   const unsigned long long limit = R->wait_limit_ns;
   unsigned long long wait_since = 0;
   uint32_t backoff = 32;
-  if (tid == 0) ctl.acc_wait = ctl.acc_stage = ctl.acc_plan = 0ull;
+  if (tid == 0) {
+    ctl.acc_wait = ctl.acc_stage = ctl.acc_plan = 0ull;
+    ctl.pf_tenant = -1;
+    ctl.args_of = -1;
+  }
 
   for (;;) {
     if (tid == 0) {
       ctl.action = kActWait;
       ctl.tenant = -1;
+      ctl.own = 0;
       bool idle = false;
       if (ld_relaxed(reinterpret_cast<uint32_t*>(&R->error)) != 0) {
         ctl.action = kActExit;
+      } else if (ctl.pf_tenant >= 0) {
+        // run the slice claimed ahead (its blocks are this CTA's now) and
+        // claim the one after it again while it runs
+        ctl.action = kActRun;
+        ctl.tenant = ctl.pf_tenant;
+        ctl.g0 = ctl.pf_g0;
+        ctl.g1 = ctl.pf_g1;
+        ctl.own = ctl.pf_more;  // a re-plan since: this slice, then the phase again
+        ctl.pf_tenant = -1;
       } else {
         const uint32_t seq = ld_acquire(&R->phase_seq);
         PhaseDev* pp = phase(P, R, seq);  // published by another CTA: read through L2
@@ -606,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
               const int32_t c = __ldcg(&pp->chain[f]);
               if (c < 0) break;
               uint32_t g0 = 0, g1 = 0;
-              if (try_pull<TC>(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
+              if (try_pull(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
                 ctl.action = kActRun;
                 ctl.tenant = c;
                 ctl.g0 = g0;
@@ -622,12 +649,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
             const uint32_t rank1 = mine_is_b ? slot - ph.slots_a : slot;
             const uint32_t rank2 = mine_is_b ? slot : slot + (S - ph.slots_a);
             uint32_t g0 = 0, g1 = 0;
-            int r = try_pull<TC>(T, R, t1, rank1, n_sm, g0, g1);
+            int r = try_pull(T, R, t1, rank1, n_sm, g0, g1);
             if (r == kPulled) {
               ctl.action = kActRun;
               ctl.tenant = t1;
               ctl.g0 = g0;
               ctl.g1 = g1;
+              ctl.own = 1;
+              ctl.own_seq = seq;
             } else {
               if (r == kExhausted) {
                 need_replan = true;
@@ -640,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
                 ctl.seq = seq;
                 ctl.trigger = trig;
               } else if (t2 >= 0) {
-                int r2 = try_pull<TC>(T, R, t2, rank2, n_sm, g0, g1);
+                int r2 = try_pull(T, R, t2, rank2, n_sm, g0, g1);
                 if (r2 == kPulled) {
                   ctl.action = kActRun;
                   ctl.tenant = t2;
@@ -667,7 +696,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
               const int32_t c = __ldcg(&pp->fill[f]);
               if (c < 0) break;
               uint32_t g0 = 0, g1 = 0;
-              if (try_pull<TC>(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
+              if (try_pull(T, R, c, 0u, n_sm, g0, g1) == kPulled) {
                 ctl.action = kActRun;
                 ctl.tenant = c;
                 ctl.g0 = g0;
@@ -708,6 +737,30 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
       const uint32_t type = d.type;
       uint32_t g = ctl.g0;
       const uint32_t g1 = ctl.g1;
+      static_assert(KL_MAX_ARGS_BYTES % 16 == 0 && offsetof(TenantDev, args) % 16 == 0, "argument copy");
+      if (ctl.args_of != ctl.tenant) {  // uniform: read after the barrier that published the action
+        if (tid < (int)(KL_MAX_ARGS_BYTES / 16))
+          reinterpret_cast<uint4*>(s_args)[tid] = __ldcg(reinterpret_cast<const uint4*>(d.args) + tid);
+        __syncthreads();
+        if (tid == 0) ctl.args_of = ctl.tenant;
+      }
+      // Claim-ahead (batch runs): a slot running its own kernel of the phase
+      // claims that kernel's next slice now and reads the claim after this
+      // slice, so the atomic's round trip overlaps the blocks instead of
+      // preceding the next slice. Only while the kernel has many slices left
+      // (the spread rule matters only near its end) and for one-stage kernels
+      // (no stage barrier between the two slices). The phase number is read
+      // alongside: after a re-plan the slot runs the slice it already owns and
+      // then reads the new phase. A serving run reads the phase before every
+      // slice instead: that is where arrivals are noticed.
+      uint32_t pf_a = 0xffffffffu, pf_seq = 0;  // the only values held across the blocks
+      if (tid == 0 && ctl.own && !R->serve && d.nstages == 1u) {
+        const uint32_t sl = d.slice;
+        if ((uint64_t)g1 + 2ull * S * n_sm * sl < (uint64_t)d.total) {
+          pf_a = atomicAdd(&d.next, sl);
+          pf_seq = ld_relaxed(&R->phase_seq);
+        }
+      }
       while (g < g1) {
         const tn::Stage st = stage_at(d, type, g);
         if (st.begin > 0) {
@@ -732,10 +785,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
         }
         const uint32_t ge = min(g1, st.end);
         const tn::BlockCtx cx{&s_tmem, &R->error, limit};
-        for (uint32_t b = g; b < ge; ++b) {
-          tn::run_block<TC>(type, d.args, st, b, smem, cx);
-          __syncthreads();  // shared memory is reused by the next block
-        }
+        tn::run_slice<BUILD>(type, s_args, st, g, ge, smem, cx);  // ends with a CTA barrier
         if (tid == 0) {
           // a later stage reads what this one wrote: release before counting
           if (d.nstages > 1) __threadfence();
@@ -745,10 +795,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
         }
         g = ge;
       }
+      if (tid == 0 && pf_a != 0xffffffffu && pf_a < d.total) {
+        const uint32_t total = d.total;
+        ctl.pf_tenant = ctl.tenant;
+        ctl.pf_g0 = pf_a;
+        ctl.pf_g1 = min(pf_a + d.slice, total);
+        ctl.pf_more = pf_seq == ctl.own_seq;
+        if (ctl.pf_g1 == total) d.drained = 1u;
+        atomicAdd(&d.slices, 1u);
+      }
     }
     __syncthreads();
   }
-  if constexpr (TC) tn::release_tmem(tcx);
+  if constexpr (BUILD == tn::kBuildFull) tn::release_tmem(tcx);
   if (tid == 0) {
     atomicAdd(&R->wait_ns, ctl.acc_wait);
     atomicAdd(&R->stage_wait_ns, ctl.acc_stage);
@@ -759,26 +818,37 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) cosched_kernel(TenantDev
 
 // ------------------------------------------------------------------ host side
 
-template <bool TC>
+template <int BUILD>
 static int occupancy_of(int* ctas_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(cosched_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tn::kMaxTenantSmem);
+  const uint32_t smem = BUILD == tn::kBuildLight ? tn::kMaxLightSmem : tn::kMaxTenantSmem;
+  cudaError_t e =
+      cudaFuncSetAttribute(cosched_kernel<BUILD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return -1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, cosched_kernel<TC>, kThreads, tn::kMaxTenantSmem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, cosched_kernel<BUILD>, kThreads, smem);
   return e == cudaSuccess ? 0 : -1;
 }
 
-int cosched_occupancy(int* ctas_per_sm, bool tensor_cores) {
-  return tensor_cores ? occupancy_of<true>(ctas_per_sm) : occupancy_of<false>(ctas_per_sm);
+int cosched_occupancy(int* ctas_per_sm, int build) {
+  switch (build) {
+    case tn::kBuildPlain: return occupancy_of<tn::kBuildPlain>(ctas_per_sm);
+    case tn::kBuildFull: return occupancy_of<tn::kBuildFull>(ctas_per_sm);
+    case tn::kBuildLight: return occupancy_of<tn::kBuildLight>(ctas_per_sm);
+    default: return -1;
+  }
 }
 
 int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
-                   bool tensor_cores, cudaStream_t stream) {
+                   int build, cudaStream_t stream) {
   dim3 grid(n_sm * slots), block(kThreads);
-  if (tensor_cores)
-    cosched_kernel<true><<<grid, block, smem_bytes, stream>>>(T, R, P);
-  else
-    cosched_kernel<false><<<grid, block, smem_bytes, stream>>>(T, R, P);
+  switch (build) {
+    case tn::kBuildPlain: cosched_kernel<tn::kBuildPlain><<<grid, block, smem_bytes, stream>>>(T, R, P); break;
+    case tn::kBuildFull: cosched_kernel<tn::kBuildFull><<<grid, block, smem_bytes, stream>>>(T, R, P); break;
+    case tn::kBuildLight:
+      if (smem_bytes > tn::kMaxLightSmem) return -1;
+      cosched_kernel<tn::kBuildLight><<<grid, block, smem_bytes, stream>>>(T, R, P);
+      break;
+    default: return -1;
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -9,7 +9,7 @@ namespace kl {
 constexpr int kThreads = KL_BLOCK_THREADS;
 constexpr int kMaxSM = 256;
 constexpr int kNoTenant = -1;
-constexpr int kFill = 8;      // backfill candidates per phase (4 unless KL_CFG_WIDE_FILL)
+constexpr int kFill = 16;     // backfill candidates per phase, at most (see replan)
 
 // One submitted kernel in device memory (128-byte aligned, 256 bytes).
 // Static fields are written by the host before the launch; dynamic fields are
@@ -53,7 +53,7 @@ struct PhaseDev {
   uint32_t pad2;
   int32_t chain[2];            // lowest pending multi-stage kernels outside A, B (chain lane)
 };
-static_assert(sizeof(PhaseDev) == 112, "PhaseDev layout");
+static_assert(sizeof(PhaseDev) == 144, "PhaseDev layout");
 
 // Serving mode: per-kernel completion record in mapped host memory, written
 // by the device before the kernel's entry in the completion queue.

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) native_kernel(ArgsBlob args, uint32_
   const tn::Stage st{stage, 0u, 0u};
   const tn::BlockCtx cx{&s_tmem, &g_native_error, 2000000000ull};
   if constexpr (TYPE == KL_T_GEMM_BF16) tn::acquire_tmem(cx);
-  tn::run_block<!tn::in_plain_build(TYPE)>(TYPE, args.b, st, blockIdx.x, smem, cx);
+  tn::run_block<tn::kBuildFull>(TYPE, args.b, st, blockIdx.x, smem, cx);
   if constexpr (TYPE == KL_T_GEMM_BF16) tn::release_tmem(cx);
 }
 

@@ -24,9 +24,9 @@
 #include "tenants.cuh"
 
 namespace kl {
-int cosched_occupancy(int* ctas_per_sm, bool tensor_cores);
+int cosched_occupancy(int* ctas_per_sm, int build);
 int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
-                   bool tensor_cores, cudaStream_t stream);
+                   int build, cudaStream_t stream);
 
 namespace {
 
@@ -83,7 +83,8 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
 
   int occ = 0, nsm = 0;
   int occ_tc = 0;  // also raises the tensor-core build's dynamic shared memory limit
-  if (cosched_occupancy(&occ, false) != 0 || occ < 1 || cosched_occupancy(&occ_tc, true) != 0) return KL_ECUDA;
+  if (cosched_occupancy(&occ, tn::kBuildPlain) != 0 || occ < 1 || cosched_occupancy(&occ_tc, tn::kBuildFull) != 0)
+    return KL_ECUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return KL_ECUDA;
   const uint32_t S = (uint32_t)(occ < KL_MAX_SLOTS ? occ : KL_MAX_SLOTS);
   const uint32_t n_sm = (uint32_t)(nsm < kMaxSM ? nsm : kMaxSM);
@@ -143,7 +144,8 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
     return KL_ECUDA;
   bool tc = false;
   for (uint32_t i = 0; i < n; ++i) tc |= !tn::in_plain_build(descs[i].type);
-  if (cosched_launch(dT, dR, dP, n_sm, S, tn::kMaxTenantSmem, tc, s) != 0) return KL_ECUDA;
+  if (cosched_launch(dT, dR, dP, n_sm, S, tn::kMaxTenantSmem, tc ? tn::kBuildFull : tn::kBuildPlain, s) != 0)
+    return KL_ECUDA;
   if (cudaMemcpyAsync(img.t, dT, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&img.run, dR, sizeof(RunDev), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return KL_ECUDA;

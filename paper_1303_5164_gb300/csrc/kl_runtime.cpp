@@ -28,9 +28,9 @@
 #include "tenants.cuh"
 
 namespace kl {
-int cosched_occupancy(int* ctas_per_sm, bool tensor_cores);
+int cosched_occupancy(int* ctas_per_sm, int build);
 int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
-                   bool tensor_cores, cudaStream_t stream);
+                   int build, cudaStream_t stream);
 int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s);
 namespace model {
 int pair(const kl_model_params& g, const kl_profile& pa, const kl_profile& pb, uint32_t slots, int states,
@@ -149,6 +149,7 @@ int validate_args(uint32_t type, const void* a) {
     case KL_T_STENCIL: {
       const kl_args_stencil* t = (const kl_args_stencil*)a;
       if (!t->in || !t->out || t->nx == 0 || t->ny == 0 || t->nz == 0) return KL_EINVAL;
+      if ((uint64_t)t->nx * t->ny * t->nz >= (1ull << 32)) return KL_EINVAL;  // 32-bit point index
       return KL_OK;
     }
     case KL_T_MRIQ: {
@@ -254,6 +255,8 @@ struct kl_runtime {
   int device = 0;
   cudaStream_t stream = nullptr;
   uint32_t n_sm = 0, slots = 0, occupancy = 0;
+  uint32_t slots_light = 0;   // CTAs per SM of the light build (0: not used)
+  uint32_t flight_slots = 0;  // CTAs per SM of the in-flight / last run
   uint32_t cap = 0, cap_phases = 0;
   uint32_t ring_slots = 0, phase_slots = 0;  // powers of two >= cap, cap_phases
   TenantDev* d_tenants = nullptr;
@@ -281,6 +284,7 @@ struct kl_runtime {
   kl_profile prof[KL_T_COUNT];
   bool table_valid = false;
   bool table_override = false;  // kl_set_cp_table: measured CPs instead of the model
+  uint32_t table_slots = 0;     // slots per SM the cached table was computed for
   double cp[KL_T_COUNT][KL_T_COUNT];
   uint32_t slots_a[KL_T_COUNT][KL_T_COUNT];
   uint32_t allowed[KL_T_COUNT][KL_T_COUNT];
@@ -326,11 +330,11 @@ void split_handle(kl_handle h, uint64_t* run, uint32_t* idx) {
 
 // CP table for every pair of types in `mask` (Section 4.4 model + Section 4.3
 // pruning). Cached until profiles, parameters or the type set change.
-int ensure_table(kl_runtime* rt, uint32_t mask) {
+int ensure_table(kl_runtime* rt, uint32_t mask, uint32_t S) {
   if (rt->table_override) return KL_OK;
-  if (rt->table_valid && (rt->table_types & mask) == mask) return KL_OK;
-  const uint32_t want = mask | (rt->table_valid ? rt->table_types : 0u);
-  const uint32_t S = rt->slots;
+  const bool same = rt->table_valid && rt->table_slots == S;
+  if (same && (rt->table_types & mask) == mask) return KL_OK;
+  const uint32_t want = mask | (same ? rt->table_types : 0u);
   std::vector<double> a(S), b(S), c(S), d(S);
   for (uint32_t i = 0; i < KL_T_COUNT; ++i)
     for (uint32_t j = 0; j < KL_T_COUNT; ++j) {
@@ -358,6 +362,7 @@ int ensure_table(kl_runtime* rt, uint32_t mask) {
     }
   }
   rt->table_types = want;
+  rt->table_slots = S;
   rt->table_valid = true;
   return KL_OK;
 }
@@ -475,8 +480,8 @@ int retire_serve(kl_runtime* rt) {
   }
   rt->last.n_tenants = n;
   rt->last.error = run_err;
-  rt->last.slots_per_sm = rt->slots;
-  rt->last.grid_ctas = rt->slots * rt->n_sm;
+  rt->last.slots_per_sm = rt->flight_slots;
+  rt->last.grid_ctas = rt->flight_slots * rt->n_sm;
   float ms = 0.f;
   rt->last.kernel_ns = cudaEventElapsedTime(&ms, rt->ev_k0, rt->ev_k1) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
   rt->last.run_ns = cudaEventElapsedTime(&ms, rt->ev_start, rt->ev_done) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
@@ -539,8 +544,8 @@ int retire(kl_runtime* rt) {
     rt->last.n_tenants = n;
     rt->last.n_phases = np;
     rt->last.error = run_err;
-    rt->last.slots_per_sm = rt->slots;
-    rt->last.grid_ctas = rt->slots * rt->n_sm;
+    rt->last.slots_per_sm = rt->flight_slots;
+    rt->last.grid_ctas = rt->flight_slots * rt->n_sm;
     rt->last.t_launch_ns = R.t_launch;
     rt->last.t_end_ns = R.t_end;
     rt->last.slot_wait_ns = R.wait_ns;
@@ -623,7 +628,7 @@ int serve_join(kl_runtime* rt) {
 // A slice never exceeds the kernel, and the queue counter (which can overshoot
 // by one slice per CTA when a kernel runs out) stays below 2^32.
 uint32_t clamp_slice(const kl_runtime* rt, uint32_t slice, uint32_t total) {
-  const uint64_t ctas = (uint64_t)rt->n_sm * rt->slots;
+  const uint64_t ctas = (uint64_t)rt->n_sm * std::max(rt->slots, rt->slots_light);
   uint64_t sl = std::min<uint64_t>(slice, total);
   while (sl > 1 && (uint64_t)total + sl * (ctas + 1) >= (1ull << 32)) sl >>= 1;
   return (uint32_t)std::max<uint64_t>(sl, 1);
@@ -712,7 +717,7 @@ extern "C" int kl_config_default(kl_config* c) {
   c->mem_cap_bytes = 0;
   c->alpha_p = -1.0;
   c->alpha_m = -1.0;
-  c->flags = KL_CFG_BACKFILL | KL_CFG_FILL_TYPES | KL_CFG_CHAIN_LANE | KL_CFG_WIDE_FILL;
+  c->flags = KL_CFG_BACKFILL | KL_CFG_FILL_TYPES | KL_CFG_CHAIN_LANE | KL_CFG_WIDE_FILL | KL_CFG_LIGHT_BUILD;
   c->chain_slots = 2;
   return KL_OK;
 }
@@ -795,12 +800,19 @@ extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime*
     int occ = 0;
     // the tensor-core build reaches the same residency: its CTAs give up the
     // TMEM allocation permit right after allocating (see acquire_tmem)
-    int occ_tc = 0;  // also raises the tensor-core build's dynamic shared memory limit
-    if (cosched_occupancy(&occ, false) != 0 || occ < 1 || cosched_occupancy(&occ_tc, true) != 0) goto fail_cuda;
+    int occ_tc = 0;     // also raises the tensor-core build's dynamic shared memory limit
+    int occ_light = 0;  // and the light build's
+    if (cosched_occupancy(&occ, tn::kBuildPlain) != 0 || occ < 1 ||
+        cosched_occupancy(&occ_tc, tn::kBuildFull) != 0 || cosched_occupancy(&occ_light, tn::kBuildLight) != 0)
+      goto fail_cuda;
     rt->occupancy = (uint32_t)occ;
     uint32_t s = cfg.slots_per_sm ? cfg.slots_per_sm : (uint32_t)occ;
     s = std::min<uint32_t>(std::min<uint32_t>(s, (uint32_t)occ), KL_MAX_SLOTS);
     rt->slots = s;
+    // a fixed slot count pins every run to it; otherwise runs of light types
+    // use the light build when it holds more CTAs per SM
+    const uint32_t sl = std::min<uint32_t>((uint32_t)std::max(occ_light, 0), KL_MAX_SLOTS);
+    rt->slots_light = (cfg.slots_per_sm == 0 && sl > s) ? sl : 0u;
   }
   // the device indexes tenants and phases modulo a power of two (a ring in
   // serving mode); a batch run never wraps: n <= cap tenants, <= 4 cap + 16 phases
@@ -931,20 +943,28 @@ static int launch_locked(kl_runtime* rt) {
     mask |= 1u << p.td.type;
     smem = std::max(smem, tn::smem_bytes(p.td.type));  // dynamic shared memory of this run's CTAs
   }
-  int rc = ensure_table(rt, mask);
+  // the smallest build that holds every type of the run (tn::run_block)
+  int build = (mask >> (KL_T_MATADD + 1)) != 0u ? tn::kBuildFull : tn::kBuildPlain;
+  bool all_light = true;
+  for (uint32_t t = 0; t < KL_T_COUNT; ++t)
+    if ((mask >> t) & 1u) all_light = all_light && tn::in_light_build(t);
+  if (all_light && (rt->cfg.flags & KL_CFG_LIGHT_BUILD) && rt->slots_light && !rt->table_override)
+    build = tn::kBuildLight;
+  const uint32_t S = build == tn::kBuildLight ? rt->slots_light : rt->slots;
+  int rc = ensure_table(rt, mask, S);
   if (rc) return rc;
   // device image: run state, tenants, the "plan first" phase
   RunDev& R = *rt->h_run;
   memset(&R, 0, sizeof(R));
   R.n_tenants = n;
-  R.slots = rt->slots;
+  R.slots = S;
   R.max_phases = std::min(rt->cap_phases, 4 * n + 16);
   R.n_types = KL_T_COUNT;
   R.wait_limit_ns = rt->cfg.device_wait_limit_ns;
   R.flags = rt->cfg.flags;
   R.serve = 0;
   R.plan_seed = rt->cfg.plan_seed;
-  R.chain_slots = std::max(1u, std::min(rt->cfg.chain_slots, rt->slots - 1));
+  R.chain_slots = std::max(1u, std::min(rt->cfg.chain_slots, S - 1));
   R.ring_mask = rt->ring_slots - 1;
   R.phase_mask = rt->phase_slots - 1;
   memcpy(R.cp, rt->cp, sizeof(R.cp));
@@ -967,8 +987,7 @@ static int launch_locked(kl_runtime* rt) {
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_phases, rt->h_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
-  const bool tc = (mask >> (KL_T_MATADD + 1)) != 0u;  // any type outside the plain build
-  if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, rt->slots, smem, tc, s) != 0)
+  if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, S, smem, build, s) != 0)
     rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
   if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_tenants, rt->d_tenants, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s));
@@ -983,6 +1002,7 @@ static int launch_locked(kl_runtime* rt) {
   rt->in_flight = true;
   rt->kind = kCosched;
   rt->flight_id = rt->run_id++;
+  rt->flight_slots = S;
   return KL_OK;
 }
 
@@ -1045,6 +1065,7 @@ extern "C" int kl_launch_baseline(kl_runtime* rt, int mode, uint32_t nstreams) {
   rt->in_flight = true;
   rt->kind = kBaseline;
   rt->flight_id = rt->run_id++;
+  rt->flight_slots = rt->slots;
   return KL_OK;
 }
 
@@ -1090,7 +1111,7 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
   if (mode == KL_SERVE_COSCHED) {
     rc = serve_alloc(rt);
     if (rc) return rc;
-    rc = ensure_table(rt, (1u << KL_T_COUNT) - 1u);  // arrivals may be of any type
+    rc = ensure_table(rt, (1u << KL_T_COUNT) - 1u, rt->slots);  // arrivals may be of any type
     if (rc) return rc;
     memset(rt->sm_ctl, 0, 256);
     memset(rt->sm_cq, 0, sizeof(unsigned long long) * rt->s_ring);
@@ -1130,7 +1151,8 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     uint32_t smem = tn::kMinCtaSmem;
     for (uint32_t t = 0; t < KL_T_COUNT; ++t)
       if (tn::in_plain_build(t) || tc) smem = std::max(smem, tn::smem_bytes(t));
-    if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, smem, tc, s) != 0)
+    if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, smem,
+                              tc ? tn::kBuildFull : tn::kBuildPlain, s) != 0)
       rc = KL_ECUDA;
     if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
@@ -1164,6 +1186,7 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
   rt->serve_mode = mode;
   rt->in_flight = true;
   rt->flight_id = rt->run_id++;  // kernels still pending keep their handles: they arrive first
+  rt->flight_slots = rt->slots;
   rt->s_tail = rt->s_head = rt->s_inflight = 0;
   rt->s_footprint = 0;
   rt->s_recs.clear();
@@ -1318,8 +1341,10 @@ extern "C" int kl_get_run_stats(kl_runtime* rt, kl_run_stats* out) {
   std::lock_guard<std::mutex> lk(rt->mu);
   progress(rt);
   *out = rt->last;
-  out->slots_per_sm = rt->slots;
-  out->grid_ctas = rt->slots * rt->n_sm;
+  if (out->slots_per_sm == 0) {  // no run retired yet: the plain build's
+    out->slots_per_sm = rt->slots;
+    out->grid_ctas = rt->slots * rt->n_sm;
+  }
   return KL_OK;
 }
 
@@ -1387,7 +1412,7 @@ extern "C" int kl_set_cp_table(kl_runtime* rt, const double* cp, const uint32_t*
 extern "C" int kl_get_cp_table(kl_runtime* rt, double* cp, uint32_t* slots_a, uint8_t* allowed) {
   if (!rt) return KL_EINVAL;
   std::lock_guard<std::mutex> lk(rt->mu);
-  int rc = ensure_table(rt, (1u << KL_T_COUNT) - 1);
+  int rc = ensure_table(rt, (1u << KL_T_COUNT) - 1, rt->slots);
   if (rc) return rc;
   for (uint32_t i = 0; i < KL_T_COUNT; ++i)
     for (uint32_t j = 0; j < KL_T_COUNT; ++j) {

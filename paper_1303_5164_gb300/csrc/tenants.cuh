@@ -58,7 +58,7 @@ constexpr uint32_t kBfSmem = 1024u + 2u * kBfStage + 64u;  // alignment slack, s
 constexpr uint32_t kBfTmemCols = 64;                       // FP32 accumulator: 128 lanes x 64 columns
 constexpr int kTeaPerBlock = 512;        // 64-bit blocks (two per thread, one 16-byte load)
 constexpr int kSadPerBlock = 256;        // SAD values (one per thread)
-constexpr int kStencilPerBlock = 256;    // x-points of one row
+constexpr int kStencilPerBlock = 256;    // consecutive points (x fastest) of a block
 constexpr int kMriqPerBlock = 256;       // k-samples (stage 0) or image points (stage 1)
 
 __host__ __device__ inline uint32_t bitonic_tile_log2(uint32_t L) {
@@ -117,7 +117,7 @@ __host__ __device__ inline uint32_t stage_blocks(uint32_t type, const void* a, u
     }
     case KL_T_STENCIL: {
       const kl_args_stencil* t = (const kl_args_stencil*)a;
-      return cdiv64(t->nx, kStencilPerBlock) * t->ny * t->nz;
+      return cdiv64((uint64_t)t->nx * t->ny * t->nz, kStencilPerBlock);
     }
     case KL_T_MRIQ: {
       const kl_args_mriq* m = (const kl_args_mriq*)a;
@@ -155,10 +155,34 @@ __host__ __device__ inline Stage stage_of(uint32_t type, const void* a, uint32_t
 }
 
 
-// Types the plain co-scheduler build runs; the others need the full build.
+// Co-scheduler builds. Every tenant body compiled into the persistent kernel
+// shares its register budget, so each run uses the build that carries only
+// the types it holds:
+//   kBuildPlain: the first ten types; 4 CTAs x 256 threads per SM, 64 registers.
+//   kBuildFull:  every type (adds the tcgen05 GEMM, TEA, SAD, stencil, MRI-Q).
+//   kBuildLight: short memory- or issue-bound bodies that fit 32 registers
+//                without shared memory beyond 256 B; 8 CTAs x 256 threads per
+//                SM, the 64 warps these kernels reach as plain launches
+//                (latency-bound ones such as SpMV and the stencil need them to
+//                keep enough loads in flight). Left out although they compile
+//                to 32 registers or fewer as plain launches: SAD and MRI-Q (their
+//                inner loops spill at 32 registers inside the co-scheduler and
+//                ran 7-12% slower than at 4 slots) and the pointer chase (64 long
+//                blocks per kernel: a pair and its fill list leave most of 8
+//                slots per SM idle).
+enum : int { kBuildPlain = 0, kBuildFull = 1, kBuildLight = 2 };
 __host__ __device__ constexpr bool in_plain_build(uint32_t type) { return type <= KL_T_MATADD; }
+__host__ __device__ constexpr bool in_light_build(uint32_t type) {
+  return type == KL_T_GATHER || type == KL_T_BLACKSCHOLES || type == KL_T_SPMV_CSR || type == KL_T_TRIAD ||
+         type == KL_T_ESCAPE || type == KL_T_MATADD || type == KL_T_TEA || type == KL_T_STENCIL;
+}
+__host__ __device__ constexpr bool in_build(int build, uint32_t type) {
+  return build == kBuildFull    ? type < KL_T_COUNT
+         : build == kBuildLight ? in_light_build(type)
+                                : in_plain_build(type);
+}
 
-__host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
+__host__ __device__ constexpr uint32_t smem_bytes(uint32_t type) {
   switch (type) {
     case KL_T_GEMM_F32: return 2u * (kGemmBK * kGemmAStride + kGemmBK * kGemmBN) * 4u;  // 16.5 KB
     case KL_T_SPMV_CSR: return 256u;                                              // long-row list
@@ -170,8 +194,15 @@ __host__ __device__ inline uint32_t smem_bytes(uint32_t type) {
   }
 }
 constexpr uint32_t kMaxTenantSmem = kBfSmem;  // largest of the above (BF16 GEMM)
+constexpr uint32_t kMaxLightSmem = 2048;       // the light build's types need at most 256 B (SpMV)
 constexpr uint32_t kMinCtaSmem = 2048;         // co-scheduler CTAs always have this much (re-plan scratch)
 static_assert(256u * 32u * 4u <= kMaxTenantSmem, "smem bound");
+__host__ __device__ constexpr bool light_smem_fits() {
+  for (uint32_t t = 0; t < KL_T_COUNT; ++t)
+    if (in_light_build(t) && smem_bytes(t) > kMaxLightSmem) return false;
+  return true;
+}
+static_assert(light_smem_fits(), "every light-build type fits the light build's shared memory");
 static_assert(2u * (kGemmBK * kGemmAStride + kGemmBK * kGemmBN) * 4u <= kMaxTenantSmem, "smem bound");
 
 #ifdef __CUDACC__
@@ -978,13 +1009,14 @@ __device__ __forceinline__ void sad_block(const kl_args_sad& a, uint32_t vb) {
 // rounded, then one fused multiply-add); boundary points are copied.
 
 __device__ __forceinline__ void stencil_block(const kl_args_stencil& a, uint32_t vb) {
-  const uint32_t bpr = (a.nx + kStencilPerBlock - 1) / kStencilPerBlock;
-  const uint32_t row = vb / bpr;
-  const uint32_t x = (vb % bpr) * kStencilPerBlock + threadIdx.x;
-  if (x >= a.nx) return;
-  const uint32_t y = row % a.ny, z = row / a.ny;
-  const uint64_t sx = 1, sy = a.nx, sz = (uint64_t)a.nx * a.ny;
-  const uint64_t i = (uint64_t)z * sz + (uint64_t)y * sy + x;
+  // block vb: the 256 consecutive points [256 vb, 256 vb + 256) of the
+  // x-fastest grid, so every thread has a point whatever nx is (the host keeps
+  // nx * ny * nz below 2^32)
+  const uint32_t i = vb * (uint32_t)kStencilPerBlock + threadIdx.x;
+  if (i >= a.nx * a.ny * a.nz) return;
+  const uint32_t x = i % a.nx, r = i / a.nx;
+  const uint32_t y = r % a.ny, z = r / a.ny;
+  const uint32_t sx = 1, sy = a.nx, sz = a.nx * a.ny;
   const float c = __ldg(a.in + i);
   if (x == 0 || y == 0 || z == 0 || x + 1 == a.nx || y + 1 == a.ny || z + 1 == a.nz) {
     a.out[i] = c;
@@ -1301,43 +1333,162 @@ __device__ __forceinline__ A load_args(const void* p) {
   return *reinterpret_cast<const A*>(p);
 }
 
-// TC: whether this caller is the full build: the tensor-core tenant and the
-// types after it (TEA, SAD, stencil, MRI-Q). Any tcgen05 instruction in a
-// kernel makes the CUDA occupancy calculator allow one CTA per SM, and every
-// extra body adds register pressure to the shared 64-register budget, so the
-// plain build (the first ten types) carries neither.
-template <bool TC>
+// BUILD: which co-scheduler build (kBuildPlain, kBuildFull, kBuildLight) the
+// caller is; a type outside it compiles to nothing. Any tcgen05 instruction in
+// a kernel makes the CUDA occupancy calculator allow one CTA per SM, and every
+// extra body adds register pressure to the shared budget, so only the full
+// build carries the tensor-core tenant and the types after it.
+template <int BUILD>
 __device__ __forceinline__ void run_block(uint32_t type, const void* args, const Stage& st, uint32_t g,
                                           char* smem, const BlockCtx& cx) {
   const uint32_t vb = g - st.begin;
   switch (type) {
-    case KL_T_GATHER: gather_block(load_args<kl_args_gather>(args), vb); break;
-    case KL_T_BLACKSCHOLES: blackscholes_block(load_args<kl_args_blackscholes>(args), vb); break;
-    case KL_T_GEMM_F32: gemm_f32_block(load_args<kl_args_gemm_f32>(args), vb, smem); break;
-    case KL_T_SPMV_CSR: spmv_csr_block(load_args<kl_args_spmv_csr>(args), vb, smem); break;
-    case KL_T_PCHASE: pchase_block(load_args<kl_args_pchase>(args), vb); break;
-    case KL_T_TRIAD: triad_block(load_args<kl_args_triad>(args), vb); break;
-    case KL_T_HIST256: hist256_block(load_args<kl_args_hist256>(args), st.s, vb, smem); break;
-    case KL_T_ESCAPE: escape_block(load_args<kl_args_escape>(args), vb); break;
-    case KL_T_BITONIC: bitonic_block(load_args<kl_args_bitonic>(args), st.s, vb, smem); break;
-    case KL_T_MATADD: matadd_block(load_args<kl_args_matadd>(args), vb); break;
+    case KL_T_GATHER:
+      if constexpr (in_build(BUILD, KL_T_GATHER)) gather_block(load_args<kl_args_gather>(args), vb);
+      break;
+    case KL_T_BLACKSCHOLES:
+      if constexpr (in_build(BUILD, KL_T_BLACKSCHOLES))
+        blackscholes_block(load_args<kl_args_blackscholes>(args), vb);
+      break;
+    case KL_T_GEMM_F32:
+      if constexpr (in_build(BUILD, KL_T_GEMM_F32)) gemm_f32_block(load_args<kl_args_gemm_f32>(args), vb, smem);
+      break;
+    case KL_T_SPMV_CSR:
+      if constexpr (in_build(BUILD, KL_T_SPMV_CSR)) spmv_csr_block(load_args<kl_args_spmv_csr>(args), vb, smem);
+      break;
+    case KL_T_PCHASE:
+      if constexpr (in_build(BUILD, KL_T_PCHASE)) pchase_block(load_args<kl_args_pchase>(args), vb);
+      break;
+    case KL_T_TRIAD:
+      if constexpr (in_build(BUILD, KL_T_TRIAD)) triad_block(load_args<kl_args_triad>(args), vb);
+      break;
+    case KL_T_HIST256:
+      if constexpr (in_build(BUILD, KL_T_HIST256)) hist256_block(load_args<kl_args_hist256>(args), st.s, vb, smem);
+      break;
+    case KL_T_ESCAPE:
+      if constexpr (in_build(BUILD, KL_T_ESCAPE)) escape_block(load_args<kl_args_escape>(args), vb);
+      break;
+    case KL_T_BITONIC:
+      if constexpr (in_build(BUILD, KL_T_BITONIC)) bitonic_block(load_args<kl_args_bitonic>(args), st.s, vb, smem);
+      break;
+    case KL_T_MATADD:
+      if constexpr (in_build(BUILD, KL_T_MATADD)) matadd_block(load_args<kl_args_matadd>(args), vb);
+      break;
     case KL_T_GEMM_BF16:
-      if constexpr (TC) gemm_bf16_block(load_args<kl_args_gemm_bf16>(args), vb, smem, cx);
+      if constexpr (in_build(BUILD, KL_T_GEMM_BF16)) gemm_bf16_block(load_args<kl_args_gemm_bf16>(args), vb, smem, cx);
       break;
     case KL_T_TEA:
-      if constexpr (TC) tea_block(load_args<kl_args_tea>(args), vb);
+      if constexpr (in_build(BUILD, KL_T_TEA)) tea_block(load_args<kl_args_tea>(args), vb);
       break;
     case KL_T_SAD:
-      if constexpr (TC) sad_block(load_args<kl_args_sad>(args), vb);
+      if constexpr (in_build(BUILD, KL_T_SAD)) sad_block(load_args<kl_args_sad>(args), vb);
       break;
     case KL_T_STENCIL:
-      if constexpr (TC) stencil_block(load_args<kl_args_stencil>(args), vb);
+      if constexpr (in_build(BUILD, KL_T_STENCIL)) stencil_block(load_args<kl_args_stencil>(args), vb);
       break;
     case KL_T_MRIQ:
-      if constexpr (TC) mriq_block(load_args<kl_args_mriq>(args), st.s, vb, smem);
+      if constexpr (in_build(BUILD, KL_T_MRIQ)) mriq_block(load_args<kl_args_mriq>(args), st.s, vb, smem);
       break;
     default: break;
   }
+}
+
+// Runs cumulative blocks [g, ge) of one stage st of a tenant (a slice, or the
+// part of it inside one stage) in a co-scheduler CTA, with the type dispatched
+// once per slice. `args` is the CTA's shared-memory copy of the descriptor's
+// arguments, made once per slice: a block of the short tenants (the stencil's
+// 256 points) is a few hundred instructions, and a dependent global load of
+// its arguments ahead of every block was a large share of it. Bodies that use
+// shared memory or synchronise inside (BARRIER) keep a CTA barrier between
+// blocks; in the others every thread is independent of the rest, so each warp
+// goes on to the next block as soon as it is done with this one. All threads
+// have finished the slice when run_slice returns.
+template <class A, bool BARRIER, class Body>
+__device__ __forceinline__ void slice_loop(const void* args, uint32_t v0, uint32_t v1, Body&& body) {
+  for (uint32_t vb = v0; vb < v1; ++vb) {
+    body(load_args<A>(args), vb);
+    if constexpr (BARRIER) {
+      if (vb + 1u < v1) __syncthreads();  // shared memory is reused by the next block
+    }
+  }
+}
+
+template <int BUILD>
+__device__ __forceinline__ void run_slice(uint32_t type, const void* args, const Stage& st, uint32_t g, uint32_t ge,
+                                          char* smem, const BlockCtx& cx) {
+  const uint32_t v0 = g - st.begin, v1 = ge - st.begin;
+  const uint32_t s = st.s;
+  switch (type) {
+    case KL_T_GATHER:
+      if constexpr (in_build(BUILD, KL_T_GATHER))
+        slice_loop<kl_args_gather, false>(args, v0, v1, [&](const kl_args_gather& a, uint32_t vb) { gather_block(a, vb); });
+      break;
+    case KL_T_BLACKSCHOLES:
+      if constexpr (in_build(BUILD, KL_T_BLACKSCHOLES))
+        slice_loop<kl_args_blackscholes, false>(
+            args, v0, v1, [&](const kl_args_blackscholes& a, uint32_t vb) { blackscholes_block(a, vb); });
+      break;
+    case KL_T_GEMM_F32:
+      if constexpr (in_build(BUILD, KL_T_GEMM_F32))
+        slice_loop<kl_args_gemm_f32, true>(
+            args, v0, v1, [&](const kl_args_gemm_f32& a, uint32_t vb) { gemm_f32_block(a, vb, smem); });
+      break;
+    case KL_T_SPMV_CSR:
+      if constexpr (in_build(BUILD, KL_T_SPMV_CSR))
+        slice_loop<kl_args_spmv_csr, true>(
+            args, v0, v1, [&](const kl_args_spmv_csr& a, uint32_t vb) { spmv_csr_block(a, vb, smem); });
+      break;
+    case KL_T_PCHASE:
+      if constexpr (in_build(BUILD, KL_T_PCHASE))
+        slice_loop<kl_args_pchase, false>(args, v0, v1, [&](const kl_args_pchase& a, uint32_t vb) { pchase_block(a, vb); });
+      break;
+    case KL_T_TRIAD:
+      if constexpr (in_build(BUILD, KL_T_TRIAD))
+        slice_loop<kl_args_triad, false>(args, v0, v1, [&](const kl_args_triad& a, uint32_t vb) { triad_block(a, vb); });
+      break;
+    case KL_T_HIST256:
+      if constexpr (in_build(BUILD, KL_T_HIST256))
+        slice_loop<kl_args_hist256, true>(
+            args, v0, v1, [&](const kl_args_hist256& a, uint32_t vb) { hist256_block(a, s, vb, smem); });
+      break;
+    case KL_T_ESCAPE:
+      if constexpr (in_build(BUILD, KL_T_ESCAPE))
+        slice_loop<kl_args_escape, false>(args, v0, v1, [&](const kl_args_escape& a, uint32_t vb) { escape_block(a, vb); });
+      break;
+    case KL_T_BITONIC:
+      if constexpr (in_build(BUILD, KL_T_BITONIC))
+        slice_loop<kl_args_bitonic, true>(
+            args, v0, v1, [&](const kl_args_bitonic& a, uint32_t vb) { bitonic_block(a, s, vb, smem); });
+      break;
+    case KL_T_MATADD:
+      if constexpr (in_build(BUILD, KL_T_MATADD))
+        slice_loop<kl_args_matadd, false>(args, v0, v1, [&](const kl_args_matadd& a, uint32_t vb) { matadd_block(a, vb); });
+      break;
+    case KL_T_GEMM_BF16:
+      if constexpr (in_build(BUILD, KL_T_GEMM_BF16))
+        slice_loop<kl_args_gemm_bf16, true>(
+            args, v0, v1, [&](const kl_args_gemm_bf16& a, uint32_t vb) { gemm_bf16_block(a, vb, smem, cx); });
+      break;
+    case KL_T_TEA:
+      if constexpr (in_build(BUILD, KL_T_TEA))
+        slice_loop<kl_args_tea, false>(args, v0, v1, [&](const kl_args_tea& a, uint32_t vb) { tea_block(a, vb); });
+      break;
+    case KL_T_SAD:
+      if constexpr (in_build(BUILD, KL_T_SAD))
+        slice_loop<kl_args_sad, false>(args, v0, v1, [&](const kl_args_sad& a, uint32_t vb) { sad_block(a, vb); });
+      break;
+    case KL_T_STENCIL:
+      if constexpr (in_build(BUILD, KL_T_STENCIL))
+        slice_loop<kl_args_stencil, false>(args, v0, v1, [&](const kl_args_stencil& a, uint32_t vb) { stencil_block(a, vb); });
+      break;
+    case KL_T_MRIQ:
+      if constexpr (in_build(BUILD, KL_T_MRIQ))
+        slice_loop<kl_args_mriq, true>(
+            args, v0, v1, [&](const kl_args_mriq& a, uint32_t vb) { mriq_block(a, s, vb, smem); });
+      break;
+    default: break;
+  }
+  __syncthreads();
 }
 
 #endif  // __CUDACC__

@@ -90,7 +90,20 @@ def test_serving_and_tensor_map_argument_checks_without_gpu(K):
     assert tuple(sh.grid) == (6, 1, 1) and sh.nstages == 1 and sh.smem_bytes >= 48 * 1024
     cfg = K.config_default()
     assert cfg.flags & K.KL_CFG_BACKFILL and cfg.flags & K.KL_CFG_CHAIN_LANE and cfg.flags & K.KL_CFG_WIDE_FILL
+    assert cfg.flags & K.KL_CFG_LIGHT_BUILD
     assert cfg.chain_slots == 2 and cfg.age_limit_ns == 0
+
+
+def test_header_constants_match_the_binding(K):
+    # every integer #define of the public header has the same value in the binding
+    txt = open(os.path.join(ROOT, "include", "kernelet.h")).read()
+    defs = dict(re.findall(r"^#define\s+(KL_\w+)\s+\(?(-?\d+)u?\)?", txt, flags=re.M))
+    assert len(defs) >= 10
+    for name, v in defs.items():
+        if hasattr(K, name):
+            assert getattr(K, name) == int(v), name
+    flags = [n for n in defs if n.startswith("KL_CFG_")]
+    assert all(hasattr(K, n) for n in flags), [n for n in flags if not hasattr(K, n)]
 
 
 def test_ctypes_structs_match_the_header(K, tmp_path):

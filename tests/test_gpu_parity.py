@@ -26,7 +26,7 @@ CASES = {
     "gemm_bf16": dict(M=200, N=132, K=136),
     "tea": dict(n=3 * 512 + 7),                                 # odd leftover block
     "sad": dict(width=64, height=36, range=3),                  # 7056 values: 28 blocks, ragged
-    "stencil": dict(nx=300, ny=17, nz=9),                       # rows of 2 blocks, the second ragged
+    "stencil": dict(nx=300, ny=17, nz=9),                       # 45,900 points: 180 blocks, the last ragged
     "mriq": dict(numK=300, numX=1000),                          # two sample chunks, ragged point block
 }
 
@@ -242,6 +242,46 @@ def test_tensor_core_build_coschedules_bf16_with_others(K, T):
         alone = _run_alone(K, rt, t)
         for k in g:
             assert X.same_bits(alone[k], g[k]), (t.name, k)
+    rt.close()
+
+
+LIGHT = ["gather", "blackscholes", "spmv_csr", "triad", "escape", "matadd", "tea", "stencil"]
+
+
+def test_light_build_runs_light_types_at_eight_slots(K, T):
+    # a run of light types only uses the 8-CTA build; every result equals the
+    # oracle and the bits of the same kernel run alone in the 4-CTA builds
+    inps = [(nm, gen.gen_tenant(nm, 31, i, **CASES[nm])) for i, nm in enumerate(LIGHT + LIGHT[::-1])]
+    rt = _runtime(K)
+    tens = [T.make(nm, x) for nm, x in inps]
+    hs = [rt.submit(t.type, t.args, slice_blocks=2) for t in tens]
+    assert rt.drain() == 0
+    S = rt.run_stats().slots_per_sm
+    assert S == 8
+    pairs = [p for p in rt.phases() if p.A >= 0 and p.B >= 0]
+    assert pairs and all(p.slots_a + p.slots_b == S for p in pairs)
+    got = [t.fetch() for t in tens]
+    for (nm, x), g, h in zip(inps, got, hs):
+        assert rt.poll(h) == K.KL_DONE
+        X.check(nm, x, g, X.expected(nm, x))
+    rt.close()
+    rt4 = _runtime(K, flags=K.config_default().flags & ~K.KL_CFG_LIGHT_BUILD)
+    for t, g in zip(tens, got):
+        alone = _run_alone(K, rt4, t)
+        assert rt4.run_stats().slots_per_sm == 4
+        for k in g:
+            assert X.same_bits(alone[k], g[k]), (t.name, k)
+    # one kernel outside the light set puts the whole run on 4 slots
+    extra = T.make("gemm_f32", gen.gen_tenant("gemm_f32", 31, 99, **CASES["gemm_f32"]))
+    rt = _runtime(K)
+    for t in tens[:4] + [extra]:
+        rt.submit(t.type, t.args)
+    assert rt.drain() == 0
+    assert rt.run_stats().slots_per_sm == 4
+    for t, g in zip(tens[:4], got[:4]):
+        f = t.fetch()
+        for k in g:
+            assert X.same_bits(f[k], g[k]), (t.name, k)
     rt.close()
 
 
