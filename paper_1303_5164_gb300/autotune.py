@@ -2,7 +2,8 @@
 within p% (default 2%) of the unsliced execution.
 
 On this runtime a slice is the block range one persistent CTA pulls with one
-atomic. For each type the kernel runs alone in the co-scheduler with slices of
+atomic. Tuning runs in the 4-slot co-scheduler builds (the light 8-slot build
+off), where every run that mixes in a heavier type executes. For each type the kernel runs alone in the co-scheduler with slices of
 1, 2, 4, ... blocks and with one slice per CTA and stage (the fewest pulls
 that still use every slot). The paper's reference is the unsliced run and
 assumes the overhead falls as slices grow; here it does not always (very
@@ -29,7 +30,11 @@ def tune(types, p=0.02, reps=3, seed=6):
     from workloads import gen
     from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
     build.build()
-    rt = K.Runtime()
+    # one slice size per type serves every run; mixed runs (every run holding
+    # one of the heavier types) use the 4-slot builds, so tune there
+    c = K.config_default()
+    c.flags &= ~K.KL_CFG_LIGHT_BUILD
+    rt = K.Runtime(c)
     n_sm = rt.model_params().n_sm
     out = {"p": p, "n_sm": n_sm, "slices": {}, "times_us": {}, "overhead": {}, "slots_per_sm": {}}
     for i, ty in enumerate(types):
