@@ -281,6 +281,12 @@ typedef enum {
                                build with 8 CTAs per SM instead of 4, and the CP
                                table for 8 slots; needs slots_per_sm = 0 and no
                                kl_set_cp_table override; default on */
+#define KL_CFG_DEEP_FILL 256u /* batch runs: a slot that neither the co-schedule
+                               nor the backfill list can use takes a slice of
+                               the lowest kernel, in submission order, that
+                               still has blocks to hand out, so kernels with
+                               fewer slices than the GPU has slots do not leave
+                               slots idle; default on */
 #define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their

@@ -705,6 +705,31 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
               }
             }
           }
+          // deep fill (batch runs): neither the pair nor the fill list has a
+          // slice for this slot (kernels with fewer slices than the GPU has
+          // slots), so take one from the lowest kernel in submission order
+          // that still has blocks to hand out. fill_cursor moves past the
+          // prefix of drained kernels; a kernel at a stage barrier is skipped
+          // without moving it.
+          if (ctl.action == kActWait && (R->flags & KL_CFG_DEEP_FILL) && !R->serve && ph.A >= 0) {
+            const uint32_t c0 = ld_relaxed(&R->fill_cursor);
+            bool prefix = true;
+            for (uint32_t j = c0; j < R->n_tenants && j < c0 + 8u; ++j) {
+              uint32_t g0 = 0, g1 = 0;
+              const int r = try_pull(T, R, (int32_t)j, 0u, n_sm, g0, g1);
+              if (r == kPulled) {
+                ctl.action = kActRun;
+                ctl.tenant = (int32_t)j;
+                ctl.g0 = g0;
+                ctl.g1 = g1;
+                break;
+              }
+              if (r == kExhausted && prefix)
+                atomicMax(&R->fill_cursor, j + 1u);
+              else
+                prefix = false;
+            }
+          }
         }
       }
       if (ctl.action == kActWait) {

@@ -110,6 +110,7 @@ struct alignas(128) RunDev {
   unsigned long long wait_ns;        // summed over CTAs: time with nothing to pull
   unsigned long long stage_wait_ns;  // summed over CTAs: time at stage barriers inside a slice
   unsigned long long plan_ns;        // summed over CTAs: time re-planning
+  alignas(128) uint32_t fill_cursor; // deep fill: kernels below this one are all drained
   alignas(128) uint32_t sm_ticket[kMaxSM];
 };
 
