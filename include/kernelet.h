@@ -415,7 +415,7 @@ int kl_destroy(kl_runtime* rt);
  * matrix. Written to out_host (256 bytes, host memory); the caller copies them
  * to device memory and passes that address as kl_args_gemm_bf16.tmaps. Needs
  * the CUDA driver (no device work). KL_EINVAL on misaligned pointers, K not a
- * multiple of 8, or a zero size; KL_ECUDA when the driver refuses the map. */
+ * multiple of 8, or a zero size; KL_ECUDA when the CUDA driver refuses the map. */
 int kl_gemm_bf16_tensor_maps(const kl_args_gemm_bf16* args, void* out_host);
 
 /* Launch shape of a tenant (no device work). */

@@ -285,6 +285,54 @@ def test_light_build_runs_light_types_at_eight_slots(K, T):
     rt.close()
 
 
+def test_deep_fill_many_small_kernels(K, T):
+    # 96 kernels of 2-4 slices each leave most slots to deep fill; with it on
+    # and off every result equals the oracle, bit for bit the same
+    specs = [("triad", dict(n=4 * 4096 + 3)), ("gather", dict(n=3 * 1024 + 5)), ("blackscholes", dict(n=2 * 256 + 1)),
+             ("matadd", dict(n=64))]
+    inps = [(nm, gen.gen_tenant(nm, 41, i, **sz)) for i in range(24) for nm, sz in specs]
+    tens = [T.make(nm, x) for nm, x in inps]
+    got = {}
+    for deep in (True, False):
+        c = K.config_default()
+        if not deep:
+            c.flags &= ~K.KL_CFG_DEEP_FILL
+        rt = K.Runtime(c)
+        hs = [rt.submit(t.type, t.args) for t in tens]
+        assert rt.drain() == 0
+        got[deep] = [t.fetch() for t in tens]
+        for (nm, x), t, g, h in zip(inps, tens, got[deep], hs):
+            assert rt.poll(h) == K.KL_DONE
+            X.check(nm, x, g, X.expected(nm, x))
+            assert rt.stats(h).blocks == t.shape().total_blocks
+        rt.close()
+    for a, b in zip(got[True], got[False]):
+        for k in a:
+            assert X.same_bits(a[k], b[k])
+
+
+def test_claim_ahead_counts_every_slice_once(K, T):
+    # a triad of 4096 one-block slices (more than 2 x slots x SMs: the slots
+    # running it claim their next slice ahead) beside kernels that force
+    # re-plans; every block runs once and every slice is counted once
+    big_in = gen.gen_triad(43, 0, 4096 * 4096)
+    big = T.make("triad", big_in)
+    others = [(nm, gen.gen_tenant(nm, 43, i + 1, **MIX_SMALL[nm])) for i, nm in
+              enumerate(["blackscholes", "escape", "pchase", "spmv_csr"])]
+    oth = [T.make(nm, x) for nm, x in others]
+    rt = _runtime(K)
+    h = rt.submit(big.type, big.args, slice_blocks=1)
+    hs = [rt.submit(t.type, t.args) for t in oth]
+    assert rt.drain() == 0
+    st = rt.stats(h)
+    assert st.blocks == 4096 and st.slices == 4096
+    X.check("triad", big_in, big.fetch(), X.expected("triad", big_in))
+    for (nm, x), t, hh in zip(others, oth, hs):
+        assert rt.poll(hh) == K.KL_DONE
+        X.check(nm, x, t.fetch(), X.expected(nm, x))
+    rt.close()
+
+
 @pytest.mark.parametrize("planner", ["random", "table"])
 def test_other_planners_keep_results(K, T, planner):
     # the MC comparison's random plans and an overridden CP table change only
