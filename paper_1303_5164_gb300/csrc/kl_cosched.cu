@@ -105,6 +105,8 @@ struct CtaCtl {
   int32_t pf_tenant;   // a slice claimed ahead while the previous one ran (-1: none)
   uint32_t pf_g0, pf_g1;
   uint32_t pf_more;    // the phase was still own_seq when that slice was claimed
+  uint32_t backoff;    // thread 0: current sleep between polls (ns)
+  unsigned long long wait_since;  // thread 0: start of the current wait (0: not waiting)
   int32_t args_of;     // kernel whose arguments s_args holds (-1: none)
   unsigned long long acc_wait, acc_stage, acc_plan;  // this CTA's time accounting (thread 0)
 };
@@ -576,13 +578,13 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
     if (tid == 0) atomicAdd(&R->ctas_done, 1u);
     return;
   }
-  const uint32_t slot = s_slot;
-  const uint32_t S = R->slots;
-  const uint32_t n_sm = gridDim.x / S;
-  const unsigned long long limit = R->wait_limit_ns;
-  unsigned long long wait_since = 0;
-  uint32_t backoff = 32;
+  // The loop keeps no scheduler state in registers across a slice: thread 0
+  // re-reads it from shared memory and the run state at each decision, so the
+  // tenant bodies get the registers (at the light build's 32 they spill
+  // otherwise).
   if (tid == 0) {
+    ctl.wait_since = 0ull;
+    ctl.backoff = 32u;
     ctl.acc_wait = ctl.acc_stage = ctl.acc_plan = 0ull;
     ctl.pf_tenant = -1;
     ctl.args_of = -1;
@@ -590,6 +592,10 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
 
   for (;;) {
     if (tid == 0) {
+      const uint32_t slot = s_slot;
+      const uint32_t S = R->slots;
+      const uint32_t n_sm = gridDim.x / S;
+      const unsigned long long limit = R->wait_limit_ns;
       ctl.action = kActWait;
       ctl.tenant = -1;
       ctl.own = 0;
@@ -734,20 +740,20 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
       }
       if (ctl.action == kActWait) {
         const unsigned long long now = gtimer();
-        if (wait_since == 0) wait_since = now;
+        if (ctl.wait_since == 0) ctl.wait_since = now;
         // an idle serving run waits for arrivals; its dispatcher ends the run
         const unsigned long long lim = (R->serve && idle) ? R->idle_limit_ns + limit : limit;
-        if (now - wait_since > lim) {
+        if (now - ctl.wait_since > lim) {
           set_error(R, KL_EDEVICE_TIMEOUT, 1u);
           ctl.action = kActExit;
         } else {
-          __nanosleep(backoff);
-          backoff = min(backoff * 2, 256u);
+          __nanosleep(ctl.backoff);
+          ctl.backoff = min(ctl.backoff * 2, 256u);
         }
       } else {
-        if (wait_since != 0) ctl.acc_wait += gtimer() - wait_since;
-        wait_since = 0;
-        backoff = 32;
+        if (ctl.wait_since != 0) ctl.acc_wait += gtimer() - ctl.wait_since;
+        ctl.wait_since = 0;
+        ctl.backoff = 32;
       }
     }
     __syncthreads();
@@ -780,6 +786,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
       // slice instead: that is where arrivals are noticed.
       uint32_t pf_a = 0xffffffffu, pf_seq = 0;  // the only values held across the blocks
       if (tid == 0 && ctl.own && !R->serve && d.nstages == 1u) {
+        const uint32_t S = R->slots, n_sm = gridDim.x / S;
         const uint32_t sl = d.slice;
         if ((uint64_t)g1 + 2ull * S * n_sm * sl < (uint64_t)d.total) {
           pf_a = atomicAdd(&d.next, sl);
@@ -795,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
             unsigned long long since = gtimer();
             uint32_t bo = 32;
             while (ld_acquire(&d.done) < st.begin) {
-              if (gtimer() - since > limit) {
+              if (gtimer() - since > R->wait_limit_ns) {
                 set_error(R, KL_EDEVICE_TIMEOUT, 2u);
                 ctl.wait_failed = 1;
                 break;
@@ -809,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
           if (ctl.wait_failed) break;
         }
         const uint32_t ge = min(g1, st.end);
-        const tn::BlockCtx cx{&s_tmem, &R->error, limit};
+        const tn::BlockCtx cx{&s_tmem, &R->error, R->wait_limit_ns};
         tn::run_slice<BUILD>(type, s_args, st, g, ge, smem, cx);  // ends with a CTA barrier
         if (tid == 0) {
           // a later stage reads what this one wrote: release before counting
