@@ -428,7 +428,12 @@ int kl_tenant_shape_of(uint32_t type, const void* args, uint32_t args_size, kl_t
 int kl_submit(kl_runtime* rt, const kl_kernel_desc* desc, kl_handle* out);
 
 /* Plan and start the pending set as one persistent co-scheduled launch on the
- * runtime's stream; returns without waiting. KL_EAGAIN if a run is in flight. */
+ * runtime's stream (Algorithm 1 over the whole set); returns without waiting.
+ * The launch uses the smallest co-scheduler build that holds every pending
+ * type: 4 slots per SM (plain; or full when a KL_T_GEMM_BF16, TEA, SAD,
+ * stencil or MRI-Q kernel is pending), or 8 slots per SM when every kernel is
+ * of a KL_CFG_LIGHT_BUILD type; kl_get_run_stats reports the slots the run
+ * used. KL_EAGAIN if a run is in flight. */
 int kl_launch(kl_runtime* rt);
 
 /* Serving mode: continuous batching. Algorithm 1 lets kernels join the

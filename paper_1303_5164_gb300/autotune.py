@@ -25,6 +25,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def choose_slice(times, p):
+    """Section 4.1's rule with the fastest measured run as the reference: the
+    smallest slice size whose time is within a fraction p of the fastest."""
+    tns = min(times.values())
+    return min(c for c in times if times[c] / tns - 1.0 <= p)
+
+
 def tune(types, p=0.02, reps=3, seed=6):
     import torch
     from workloads import gen
@@ -60,7 +67,7 @@ def tune(types, p=0.02, reps=3, seed=6):
 
         times = {c: run(c) for c in cands}
         tns = min(times.values())
-        chosen = min(c for c in cands if times[c] / tns - 1.0 <= p)
+        chosen = choose_slice(times, p)
         out["slices"][ty] = chosen
         out["times_us"][ty] = {str(c): round(v, 2) for c, v in times.items()}
         out["overhead"][ty] = round(times[chosen] / tns - 1.0, 4)
