@@ -69,3 +69,20 @@ def test_benchmark_and_entry_point_reach_the_oracle_only_where_allowed():
     assert not top and owners <= {"cpu_oracle_sample", "run_reference"}, owners
     owners, top = _functions_importing_oracle(os.path.join(ROOT, "__graft_entry__.py"))
     assert not top and owners <= {"build", "smoke"}, owners
+
+
+def test_product_fails_loudly_without_its_library(tmp_path):
+    # no fallback: a missing libkernelet.so raises instead of computing anything on the CPU
+    import subprocess
+    import sys
+    code = ("import paper_1303_5164_gb300.kernelet as K\n"
+            f"K.lib_path = lambda: {str(tmp_path / 'absent.so')!r}\n"
+            "K._lib = None\n"
+            "try:\n"
+            "    K.lib()\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    raise SystemExit(0)\n"
+            "raise SystemExit(1)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode == 0 and "no fallback" in r.stdout, r.stdout + r.stderr
