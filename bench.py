@@ -332,9 +332,34 @@ def _load_profiles(K, path=PROFILES):
     return profs, d
 
 
+def _oracle_one(name, inp):
+    """One tenant instance through the CPU oracle (its C loops run with the
+    GIL released, so threads calling this run on separate cores)."""
+    from oracle import tenants as OT
+    if name == "gemm_f32":
+        OT.gemm_f32(inp["A"], inp["B"])
+    elif name == "spmv_csr":
+        OT.spmv_csr(inp["rowptr"], inp["col"], inp["val"], inp["x"])
+    elif name == "blackscholes":
+        OT.blackscholes(inp["S"], inp["K"], inp["r"], inp["v"], inp["T"])
+    elif name == "pchase":
+        OT.pchase(inp["next"], inp["start"], inp["hops"])
+    elif name == "triad":
+        OT.triad(inp["b"], inp["c"], inp["s"])
+    elif name == "hist256":
+        OT.hist256(inp["data"])
+    elif name == "escape":
+        OT.escape(inp["width"], inp["height"], inp["max_iter"], inp["x0"], inp["y0"], inp["dx"], inp["dy"])
+    elif name == "bitonic":
+        OT.sort_u32(inp["data"])
+    elif name == "gather":
+        OT.gather(inp["a"], inp["idx"])
+    else:
+        raise ValueError(name)
+
+
 def cpu_oracle_sample(jobs_inputs):
     """The CPU oracle on one instance of each tenant type (single thread)."""
-    import numpy as np
     from oracle import tenants as OT
     OT.build()
     seen = {}
@@ -343,56 +368,132 @@ def cpu_oracle_sample(jobs_inputs):
             seen[name] = inp
     t0 = time.perf_counter()
     for name, inp in seen.items():
-        if name == "gemm_f32":
-            OT.gemm_f32(inp["A"], inp["B"])
-        elif name == "spmv_csr":
-            OT.spmv_csr(inp["rowptr"], inp["col"], inp["val"], inp["x"])
-        elif name == "blackscholes":
-            OT.blackscholes(inp["S"], inp["K"], inp["r"], inp["v"], inp["T"])
-        elif name == "pchase":
-            OT.pchase(inp["next"], inp["start"], inp["hops"])
-        elif name == "triad":
-            OT.triad(inp["b"], inp["c"], inp["s"])
-        elif name == "hist256":
-            OT.hist256(inp["data"])
-        elif name == "escape":
-            OT.escape(inp["width"], inp["height"], inp["max_iter"], inp["x0"], inp["y0"], inp["dx"], inp["dy"])
-        elif name == "bitonic":
-            OT.sort_u32(inp["data"])
-        elif name == "gather":
-            OT.gather(inp["a"], inp["idx"])
+        _oracle_one(name, inp)
     dt = time.perf_counter() - t0
     return len(seen), dt, sorted(seen)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_all_cores(jobs_inputs, threads: int | None = None):
+    """The CPU oracle on every instance of the batch, one instance per task on
+    a pool of `threads` host threads (all cores by default): wall time of
+    the whole batch. Returns (instances, seconds, threads)."""
+    import concurrent.futures as cf
+    from oracle import tenants as OT
+    OT.build()
+    OT.lib()  # load once, before the threads
+    threads = threads or host_cores()
+    # longest first, so the pool does not end on one long instance
+    order = sorted(range(len(jobs_inputs)), key=lambda i: jobs_inputs[i][0] != "gemm_f32")
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda i: _oracle_one(*jobs_inputs[i]), order))
+    return len(jobs_inputs), time.perf_counter() - t0, threads
+
+
+def gpu_numa_node(device: int):
+    """NUMA node of the GPU's PCI function (sysfs), or None when unknown."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(device)
+        dom, bus, dev = (getattr(p, "pci_domain_id", None), getattr(p, "pci_bus_id", None),
+                         getattr(p, "pci_device_id", None))
+        if bus is None:
+            return None
+        with open(f"/sys/bus/pci/devices/{dom or 0:04x}:{bus:02x}:{dev or 0:02x}.0/numa_node") as f:
+            n = int(f.read().strip())
+        return n if n >= 0 else None
+    except (OSError, ValueError, RuntimeError):
+        return None
+
+
+def bind_host_to_gpu_node(device: int):
+    """Run this process on the host cores of the GPU's NUMA node, so pinned
+    buffers allocated afterwards (first touched by this thread) sit in that
+    node's memory. Returns (node, cores) or (None, None) when there is no such
+    information."""
+    node = gpu_numa_node(device)
+    if node is None:
+        return None, None
+    try:
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        if not cpus:
+            return node, None
+        os.sched_setaffinity(0, cpus)
+        return node, len(cpus)
+    except (OSError, ValueError, AttributeError):
+        return node, None
+
+
+def make_runtime(K, device: int = 0, stream: int = 0, flags=None, profiles: str = "measured"):
+    """The runtime the timed co-scheduled steps use: default configuration
+    (4096 pending kernels, the library's default flags unless `flags`), the
+    measured HBM bandwidth in the model, and the measured per-type profiles
+    and fitted latency parameters. Returns (runtime, model params, model info)."""
+    cfg = K.config_default()
+    cfg.device = device
+    cfg.max_tenants = 4096
+    if flags is not None:
+        cfg.flags = flags
+    rt = K.Runtime(cfg, stream=stream)
+    hbm_gbs, _ = _measured_peaks()
+    mp_ = rt.model_params()
+    mp_.dram_bytes_per_s = hbm_gbs * 1e9
+    rt.set_model_params(mp_)
+    profs, prof_doc = _load_profiles(K, None if profiles == "none" else PROFILES)
+    model_info = {"profiles": "built-in (not measured)"}
+    if profs:
+        rt.set_profiles(profs)
+        mp_.a0, mp_.b0 = prof_doc.get("a0", 1.0), prof_doc.get("b0", 0.0)
+        rt.set_model_params(mp_)
+        model_info = {"profiles": prof_doc.get("source"), "a0": mp_.a0, "b0": mp_.b0,
+                      "solo_ipc_mae_per_sm": prof_doc.get("ipc_mae_per_sm"), "ipc_peak_per_sm": 4.0,
+                      "slices": prof_doc.get("slices")}
+    return rt, mp_, model_info
 
 
 # ---------------------------------------------------------------------- reference arm
 
 def run_reference(args):
+    """The CPU oracle as the reference arm: each step runs the whole 64-kernel
+    mix (the same kernels, sizes and order the co-scheduled arm times) on all
+    host cores, one kernel instance per thread-pool task."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     jobs = mix_jobs()
-    # one instance of each type per step (a bounded sample of the 64-kernel mix)
-    first = {}
-    for j in jobs:
-        first.setdefault(j[0], j)
-    sample = list(first.values())
-    inputs = generate(sample, min(len(sample), os.cpu_count() or 1))
-    pairs = [(j[0], x) for j, x in zip(sample, inputs)]
+    inputs = generate(jobs, max(1, min(len(jobs), host_cores())))
+    pairs = [(j[0], x) for j, x in zip(jobs, inputs)]
     for _ in range(args.warmup):
-        cpu_oracle_sample(pairs)
+        cpu_oracle_all_cores(pairs)
     times = []
     for _ in range(args.steps):
-        n, dt, _ = cpu_oracle_sample(pairs)
+        n, dt, cores = cpu_oracle_all_cores(pairs)
         times.append(dt)
     ms = 1e3 * sum(times) / len(times)
     val = n / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "kernels/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reference": "CPU oracle (oracle/tenants.c), single thread"},
-            "cpu_baseline": {"value": val, "unit": "kernels/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one instance of each of the {n} kernel types per step, full size"},
+            "config": {"workload": WORKLOAD, "kernels_per_step": n,
+                       "reference": f"CPU oracle (oracle/tenants.c) on {cores} host threads"},
+            "cpu_baseline": {"value": val, "unit": "kernels/s", "cores": cores, "kind": "oracle",
+                             "sample": f"the whole {n}-kernel mix per step, full size, one instance per "
+                                       f"task on {cores} threads"},
             "e2e": {"value": val, "unit": "kernels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -425,25 +526,8 @@ def run_ours(args):
     names = [j[0] for j in jobs]
     tens = [T.make(nm, x) for nm, x in zip(names, inputs)]
     stream = torch.cuda.current_stream()
-    cfg = K.config_default()
-    cfg.device = local
-    cfg.max_tenants = 4096
-    if args.flags is not None:
-        cfg.flags = args.flags
-    rt = K.Runtime(cfg, stream=stream.cuda_stream)
+    rt, mp_, model_info = make_runtime(K, local, stream.cuda_stream, args.flags, args.profiles)
     hbm_gbs, peak_src = _measured_peaks()
-    mp_ = rt.model_params()
-    mp_.dram_bytes_per_s = hbm_gbs * 1e9
-    rt.set_model_params(mp_)
-    profs, prof_doc = _load_profiles(K, None if args.profiles == "none" else PROFILES)
-    model_info = {"profiles": "built-in (not measured)"}
-    if profs:
-        rt.set_profiles(profs)
-        mp_.a0, mp_.b0 = prof_doc.get("a0", 1.0), prof_doc.get("b0", 0.0)
-        rt.set_model_params(mp_)
-        model_info = {"profiles": prof_doc.get("source"), "a0": mp_.a0, "b0": mp_.b0,
-                      "solo_ipc_mae_per_sm": prof_doc.get("ipc_mae_per_sm"), "ipc_peak_per_sm": 4.0,
-                      "slices": prof_doc.get("slices")}
     prof_src = model_info["profiles"]
 
     def submit_all():
@@ -522,10 +606,13 @@ def run_ours(args):
             esc_iters[id(t)] = int(t.bufs["count"].to(torch.int64).sum().item())
     bytes_mix = sum(RF.algo_bytes(nm, x) for nm, x in zip(names, inputs))
     flops_mix = sum(RF.fp32_flops(nm, x, esc_iters.get(id(t))) for nm, x, t in zip(names, inputs, tens))
+    ops_mix = sum(RF.lane_ops(nm, x, esc_iters.get(id(t))) for nm, x, t in zip(names, inputs, tens))
     kern_ms = statistics.median(kern_ns) / 1e6
     achieved = bytes_mix / (kern_ms / 1e3) / 1e9
     f_sm = (clocks.get("sm_mhz") or 1900.0) * 1e6
-    t_roof = max(bytes_mix / (hbm_gbs * 1e9), flops_mix / RF.fp32_peak_flops(mp_.n_sm, f_sm))
+    t_hbm = bytes_mix / (hbm_gbs * 1e9)
+    t_issue = ops_mix / RF.lane_peak(mp_.n_sm, f_sm)
+    t_roof = max(t_hbm, t_issue)
 
     # end to end through the public API with host buffers: H2D inputs, run, D2H outputs
     e2e = None
@@ -536,6 +623,8 @@ def run_ours(args):
         # own streams while step k computes. Every step's copies are inside
         # the timed region.
         sets = [tens, [T.make(nm, x) for nm, x in zip(names, inputs)]]
+        affinity = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
+        numa_node, numa_cores = bind_host_to_gpu_node(local)
         pin_in, pin_out = [], []
         h2d = d2h = 0
         for t in tens:
@@ -595,19 +684,50 @@ def run_ours(args):
 
         e2e_run(2)
         ms_e2e = e2e_run(max(4, args.steps))
+
+        def copy_gbs(upload_dir):
+            # one step's copies alone, on one stream: the link's achieved rate
+            q = torch.cuda.Stream()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            c0.record(q)
+            with torch.cuda.stream(q):
+                for t, ins, outs in zip(tens, pin_in, pin_out):
+                    if upload_dir:
+                        for k, v in ins.items():
+                            t.bufs[k].copy_(v, non_blocking=True)
+                    else:
+                        for k, v in outs.items():
+                            v.copy_(t.bufs[k], non_blocking=True)
+            c1.record(q)
+            c1.synchronize()
+            return (h2d if upload_dir else d2h) / (c0.elapsed_time(c1) / 1e3) / 1e9
+
+        h2d_gbs, d2h_gbs = copy_gbs(True), copy_gbs(False)
         e2e = {"value": job_value(n, world, ms_e2e), "unit": "kernels/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+               "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs,
+               "host_numa_node": numa_node, "host_cores_bound": numa_cores,
                "how": "public API (kl_submit/kl_launch/kl_drain) on pinned host buffers; uploads and downloads on "
-                      "their own streams, overlapping the neighbouring steps' compute (two device buffer sets)"}
+                      "their own streams, overlapping the neighbouring steps' compute (two device buffer sets); "
+                      "pinned buffers allocated with the process bound to the GPU's NUMA node (when sysfs "
+                      "names one); *_gbs_alone = one step's copies in one direction, alone on one stream"}
         del sets, pin_in, pin_out
+        if affinity is not None:
+            os.sched_setaffinity(0, affinity)
         torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        k, dt, kinds = cpu_oracle_sample(list(zip(names, inputs)))
-        cpu = {"value": k / dt, "unit": "kernels/s", "cores": 1, "kind": "oracle",
-               "sample": f"one full-size instance of each of the {k} kernel types ({', '.join(kinds)}), "
-                         f"single thread, {dt:.1f} s"}
+        pairs = list(zip(names, inputs))
+        k, dt, cores = cpu_oracle_all_cores(pairs)
+        k1, dt1, kinds = cpu_oracle_sample(pairs)
+        cpu = {"value": k / dt, "unit": "kernels/s", "cores": cores, "kind": "oracle",
+               "sample": f"the whole {k}-kernel mix, full size, one instance per task on {cores} host "
+                         f"threads, {dt:.1f} s",
+               "single_thread": {"value": k1 / dt1, "unit": "kernels/s", "cores": 1,
+                                 "sample": f"one full-size instance of each of the {k1} kernel types "
+                                           f"({', '.join(kinds)}), {dt1:.1f} s"}}
 
     if rank == 0:
         line = {
@@ -624,7 +744,10 @@ def run_ours(args):
             "latency_ms": {"cosched_p50": _pct(lat_co, 50), "cosched_p99": _pct(lat_co, 99),
                            "multistream_p50": _pct(lat_ms, 50), "multistream_p99": _pct(lat_ms, 99)},
             "mix_roofline": {"t_roof_ms": t_roof * 1e3, "frac": (t_roof * 1e3) / kern_ms,
-                             "algo_bytes": bytes_mix, "fp32_flops": flops_mix},
+                             "t_hbm_ms": t_hbm * 1e3, "t_issue_ms": t_issue * 1e3,
+                             "algo_bytes": bytes_mix, "lane_ops": ops_mix, "fp32_flops": flops_mix,
+                             "how": "T_roof = max(sum of algorithmic bytes / measured HBM, sum of lane "
+                                    "operations / (SMs x 128 lanes x sampled SM clock))"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
                          "frac": achieved / hbm_gbs, "traffic": _measured_traffic(args.workload),
                          "kernel": "cosched_kernel", "kernel_ms": kern_ms,

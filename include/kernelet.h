@@ -397,16 +397,25 @@ typedef enum {
 
 /* ------------------------------------------------------------------ runtime */
 
-/* Fill `cfg` with defaults. */
+/* Fill `cfg` with defaults (no counterpart in the paper: library
+ * housekeeping). KL_EINVAL on NULL. */
 int kl_config_default(kl_config* cfg);
 
-/* Create a runtime on cfg->device that launches on `cuda_stream` (a
- * cudaStream_t, may be NULL for the legacy default stream). Allocates the
- * device queue (cfg->max_tenants descriptors) and pinned host staging. */
+/* Create a runtime: the kernel queue and scheduler of Section 3.2 (Fig.
+ * kerneletOverview: kernels are buffered in a queue, the scheduler picks the
+ * co-schedules, slices are dispatched to the GPU) for one GPU, cfg->device,
+ * launching on `cuda_stream` (a cudaStream_t, may be NULL for the legacy
+ * default stream). cfg NULL = kl_config_default. Allocates the device queue
+ * (cfg->max_tenants descriptors) and pinned host staging; the runtime owns
+ * them until kl_destroy. *out receives the handle (host memory).
+ * Errors: KL_EINVAL (NULL out, bad device or sizes), KL_ENOMEM, KL_ECUDA. */
 int kl_create(const kl_config* cfg, void* cuda_stream, kl_runtime** out);
 
-/* Wait for in-flight work (up to the device wait limit), free everything.
- * KL_ESTATE if a run could not be retired. */
+/* End of the runtime of Section 3.2: wait for in-flight work (up to the
+ * device wait limit; a serving run is stopped first), then free the queue,
+ * staging and history. Handles of this runtime become invalid. KL_ESTATE if a
+ * run could not be retired (its memory is then left allocated); KL_EINVAL on
+ * NULL. */
 int kl_destroy(kl_runtime* rt);
 
 /* Tensor maps (two CUtensorMap, 128 bytes each: A then Bt) that the
@@ -426,6 +435,22 @@ int kl_tenant_shape_of(uint32_t type, const void* args, uint32_t args_size, kl_t
  * Non-blocking; copies the descriptor and arguments. KL_EAGAIN when the
  * pending set is full or over the memory cap. */
 int kl_submit(kl_runtime* rt, const kl_kernel_desc* desc, kl_handle* out);
+
+/* Staged arrival (Algorithm 1, "a new kernel comes", for a burst of kernels):
+ * kl_submit_staged admits a kernel like kl_submit but, while serving, does
+ * not make it visible to the device: the descriptor is written into the
+ * mapped ring (co-scheduled) or held back (plain launches) and the kernel
+ * stays KL_PENDING. kl_publish makes every staged kernel visible with one
+ * release store of the ring's tail, so the device takes the whole burst in
+ * and re-plans once instead of once per kernel; a kl_submit publishes every
+ * kernel staged before it too. A serving run stopped (kl_serve_stop) while
+ * kernels are still staged never runs them: they end in KL_ERROR (error
+ * KL_ESTATE), their buffers untouched. Outside serving, kl_submit_staged is
+ * kl_submit (the next kl_launch takes every pending kernel) and kl_publish
+ * returns KL_OK. Errors as kl_submit; kl_publish: KL_EINVAL on NULL,
+ * KL_ECUDA when a held-back plain launch fails. */
+int kl_submit_staged(kl_runtime* rt, const kl_kernel_desc* desc, kl_handle* out);
+int kl_publish(kl_runtime* rt);
 
 /* Plan and start the pending set as one persistent co-scheduled launch on the
  * runtime's stream (Algorithm 1 over the whole set); returns without waiting.
@@ -481,30 +506,68 @@ int kl_reap(kl_runtime* rt, kl_handle* out, uint32_t cap, uint32_t* n);
  * on it bracket the whole run. Returns without waiting. */
 int kl_launch_baseline(kl_runtime* rt, int mode, uint32_t nstreams);
 
-/* Current state of a handle (kl_state) without blocking. */
+/* Current state of a handle (kl_state) into *state, without blocking.
+ * Algorithm 1 removes a kernel from the pending set R once all its thread
+ * blocks have executed (Section 2.2: every block occurs in one co-schedule
+ * once); DONE is that moment, RUNNING means some of its slices have been
+ * dispatched. Retires a finished run as a side effect. KL_ENOTFOUND for a
+ * handle this runtime never issued (or whose record was dropped). */
 int kl_poll(kl_runtime* rt, kl_handle h, int* state);
 
-/* Block until the handle is DONE/ERROR or timeout_ns elapses (KL_ETIMEDOUT). */
+/* Block until the handle is DONE or ERROR (the end of that kernel in
+ * Algorithm 1's loop), or until timeout_ns elapses: KL_ETIMEDOUT, and the
+ * kernel keeps running (timeout_ns = 0 only polls). Returns KL_OK when the
+ * kernel completed, its error when it failed, KL_ENOTFOUND for an unknown
+ * handle, KL_ESTATE for a kernel still in R that no launch has started
+ * (waiting for it would never end). */
 int kl_wait(kl_runtime* rt, kl_handle h, uint64_t timeout_ns);
 
-/* Launch whatever is pending, then wait for the whole run; returns the run's
- * status (KL_OK, KL_EDEVICE_TIMEOUT, ...). */
+/* Algorithm 1 run to the end: launch whatever is pending (the outer loop
+ * "while R != null"), then wait until every kernel of the run is DONE or
+ * ERROR, or timeout_ns elapses (KL_ETIMEDOUT; the run continues and a later
+ * kl_drain waits again). Returns the run's status (KL_OK, KL_EDEVICE_TIMEOUT,
+ * KL_EOVERFLOW, ...); KL_ESTATE while serving. */
 int kl_drain(kl_runtime* rt, uint64_t timeout_ns);
 
+/* Per-kernel measurements of a finished or running kernel (host memory out):
+ * submit, start and end times, slices pulled and blocks executed. The start
+ * and end stamps give the kernel's execution time within the scheduling plan
+ * (Section 2.2: the total execution time is the objective). KL_ENOTFOUND for
+ * an unknown handle. */
 int kl_get_stats(kl_runtime* rt, kl_handle h, kl_tenant_stats* out);
+
+/* Statistics of the last retired run (host memory out): its kernel time, the
+ * co-schedules chosen, and the idle, stage-barrier and planning time summed
+ * over the CTAs (the scheduling overhead Section 3.1 asks to keep small).
+ * KL_EINVAL on NULL. */
 int kl_get_run_stats(kl_runtime* rt, kl_run_stats* out);
 
-/* Phase log (the co-schedules the device chose) of the last retired run. */
+/* Phase log of the last retired run: the sequence of co-schedules
+ * <K1, K2, size1, size2> that Algorithm 1 chose, in order (the scheduling
+ * plan of Section 2.2), up to cap entries into out (host memory; may be NULL
+ * when cap = 0); *n receives the number of phases the run logged, which may
+ * exceed cap. */
 int kl_get_phases(kl_runtime* rt, kl_phase* out, uint32_t cap, uint32_t* n);
 
-/* Model inputs: per-type profiles and GPU parameters. Changing them
- * invalidates the cached CP table. */
+/* Model inputs. kl_set_profiles: per-type profile (Table 1's R_m, the
+ * uncoalesced fraction and sectors per access of Section 4.4 "uncoalesced
+ * access", instructions per block, PUR and MUR of Section 4.3), measured by
+ * profiling the kernel (Section 4.4, "getting the input"); profiles[t] is
+ * type t, n_types <= KL_T_COUNT, copied. kl_set_model_params: the GPU
+ * parameters of the virtual SM (Section 4.4, "multiple warp schedulers":
+ * schedulers per SM; DRAM bandwidth and clock for B; the linear latency
+ * parameters a0, b0 of the latency equation). Changing either invalidates the
+ * cached CP table. KL_EINVAL on NULL or out-of-range values. */
 int kl_set_profiles(kl_runtime* rt, const kl_profile* profiles, uint32_t n_types);
 int kl_set_model_params(kl_runtime* rt, const kl_model_params* params);
 int kl_get_model_params(kl_runtime* rt, kl_model_params* out);
 
-/* CP table the device planner uses: cp[i*KL_T_COUNT+j] and slots for the
- * first kernel of a (type i, type j) pair at `slots` slots per SM. */
+/* CP table the device planner uses (Eq. cp from the Section 4.4 model, one
+ * entry per type pair, the pruning of Section 4.3 in `allowed`):
+ * cp[i*KL_T_COUNT+j] and slots for the first kernel of a (type i, type j)
+ * pair at the runtime's slots per SM (the balanced ratio, Eq.
+ * executiontime). Arrays of KL_T_COUNT^2 entries, host memory; any may be
+ * NULL. */
 int kl_get_cp_table(kl_runtime* rt, double* cp, uint32_t* slots_a, uint8_t* allowed);
 
 /* Replace the model's table with given values (the OPT comparison of Section
@@ -552,21 +615,27 @@ int kl_count_pruned(const double* pur, const double* mur, uint32_t n, double alp
  * call cudaMalloc / cudaFree because those calls can synchronize the device.
  *
  * kl_run_noalloc runs descs[0..n) as ONE co-scheduled launch of the same
- * persistent kernel as kl_launch and waits for it on `cuda_stream` (a
- * cudaStream_t, may be NULL). It calls no cudaMalloc, cudaFree or other
- * allocating routine: the device queue, run state and phase log live in a
- * fixed file-scope device array of the library (about 37 KB, held by every
- * GPU that loads the library until the process exits), and the host-side
- * descriptor image lives on the caller's stack (about 19 KB).
+ * persistent kernel as kl_launch on `cuda_stream` (a cudaStream_t, may be
+ * NULL) and returns after the run has completed: it synchronizes that stream.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the device
+ * queue, run state and phase log live in a fixed file-scope device array of
+ * the library (KL_NOALLOC_SCRATCH_BYTES = 95,232 bytes, held by every GPU that
+ * loads the library until the process exits), and the host-side descriptor
+ * image lives on the caller's stack (about 21.5 KB).
  *   descs, n        kernel descriptors as for kl_submit; 1 <= n <=
- *                   KL_NOALLOC_MAX_TENANTS, else KL_EOVERFLOW (n = 0: KL_EINVAL)
+ *                   KL_NOALLOC_MAX_TENANTS, else KL_EOVERFLOW (n = 0: KL_EINVAL);
+ *                   slice_blocks = 0 takes the runtime's built-in slice of the
+ *                   type (no profiles are loaded here)
  *   cp_table        NULL, or KL_T_COUNT x KL_T_COUNT CP values by (type of the
  *                   lower-index kernel, type of the other) for the device planner;
  *                   NULL = all equal (pairs in submission order)
  *   slots_a_table   NULL, or slots per SM for the lower-index kernel of each
  *                   type pair (clamped to 1..slots-1); NULL = even split
  *   wait_limit_ns   bound of every device-side wait (0 = 2 s)
- *   states          NULL, or n entries receiving KL_DONE / KL_ERROR per kernel
+ *   states          NULL, or n entries receiving KL_DONE / KL_ERROR per kernel;
+ *                   left untouched when the call returns an error before the
+ *                   run's results are read back (a bad descriptor,
+ *                   KL_EOVERFLOW, a failed CUDA call)
  * Returns KL_OK when every kernel completed, else a kl_status.
  * The first call on each device takes the device address of the array
  * (cudaGetSymbolAddress) with that device current; make that first call before
@@ -574,11 +643,14 @@ int kl_count_pruned(const double* pur, const double* mur, uint32_t n, double alp
  * call's contents (each call rewrites what must start at zero); calls whose
  * GPU work overlaps race on it and must not be issued concurrently. */
 #define KL_NOALLOC_MAX_TENANTS 64
+#define KL_NOALLOC_SCRATCH_BYTES 95232
 int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const double* cp_table,
                    const uint32_t* slots_a_table, void* cuda_stream, uint64_t wait_limit_ns,
                    int32_t* states);
 
+/* Static text for a kl_status (no counterpart in the paper). */
 const char* kl_strerror(int code);
+/* KL_ABI_VERSION of the library that was loaded (no counterpart in the paper). */
 int kl_abi_version(void);
 
 #ifdef __cplusplus

@@ -107,6 +107,17 @@ def gemm_f32_sample(A, B, ii, jj):
     return out
 
 
+def gemm_f32_exact(A, B):
+    """The definition's exact value C = A B for binary32 inputs, in binary64
+    (one library matmul; each product of two binary32 values is exact in
+    binary64), and sum_k |a_ik b_kj|, the scale of the binary32 chain's
+    rounding error: |C_chain - C| <= K 2^-24 sum_k |a_ik b_kj| per entry.
+    For checking GEMMs too large for the chain loop, entry by entry."""
+    a = np.asarray(A, dtype=np.float64)
+    b = np.asarray(B, dtype=np.float64)
+    return a @ b, np.abs(a) @ np.abs(b)
+
+
 def bf16_to_f64(bits):
     """Value of bfloat16 bit patterns: the upper half of a binary32 word."""
     b = np.ascontiguousarray(bits, dtype=np.uint16)

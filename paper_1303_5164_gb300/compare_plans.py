@@ -11,7 +11,8 @@ Each planner runs the mix with the library's default flags (backfill, chain
 lane: what the bench runs) and with flags 0 (pure pairs: the planner alone
 decides what shares the GPU). Reported: co-scheduler kernel time (median of
 runs for Kernelet and OPT; every run for MC), and where Kernelet falls in the
-MC distribution.
+MC distribution. Every run's outputs are compared bit for bit with the
+kernels' plain launches.
 
     python -m paper_1303_5164_gb300.compare_plans --out plans.json [--mc 1000]
 """
@@ -133,15 +134,32 @@ def run(out_path, mc=1000, mc_pure=200, reps=5):
     # the model's table, for the record
     cp_model, sl_model, _ = runtime().cp_table()
 
-    # ---- the mix under each planner
+    # ---- the mix under each planner; every planner must leave every output
+    # equal (on the device, bit for bit) to the kernel's plain launch
+    rt = runtime()
+    for t in tens:
+        for k in t.outputs:
+            t.bufs[k].fill_(-1)
+        rt.submit(t.type, t.args)
+    rt.launch_baseline(K.KL_BASE_SERIAL, 1)
+    assert rt.drain() == 0
+    rt.close()
+    ref = [{k: t.bufs[k].clone() for k in t.outputs} for t in tens]
+
     def mix_time(rt, n=reps):
         ts = []
         for _ in range(n):
             for t in tens:
+                for k in t.outputs:
+                    t.bufs[k].fill_(-1)
                 rt.submit(t.type, t.args)
             rt.launch()
             assert rt.drain() == 0
             ts.append(rt.run_stats().kernel_ns / 1e6)
+            for t, r in zip(tens, ref):
+                for k, v in r.items():
+                    if not torch.equal(t.bufs[k], v):
+                        raise AssertionError(f"{t.name}.{k}: output differs from the plain launch")
         return ts
 
     res = {"slots_per_sm": S, "cp_measured": {f"{a}+{b}@{sa}": v for (a, b, sa), v in cp_meas.items()},

@@ -11,6 +11,30 @@ constexpr int kMaxSM = 256;
 constexpr int kNoTenant = -1;
 constexpr int kFill = 16;     // backfill candidates per phase, at most (see replan)
 
+// Pull granularity per type (blocks per slice) when the descriptor leaves it to
+// the runtime; chosen so one atomic covers roughly 16-64 KB of traffic or one
+// long block.
+inline uint32_t default_slice(uint32_t type) {
+  switch (type) {
+    case KL_T_GATHER: return 4;
+    case KL_T_BLACKSCHOLES: return 8;
+    case KL_T_GEMM_F32: return 1;
+    case KL_T_SPMV_CSR: return 8;
+    case KL_T_PCHASE: return 1;
+    case KL_T_TRIAD: return 2;
+    case KL_T_HIST256: return 2;
+    case KL_T_ESCAPE: return 8;
+    case KL_T_BITONIC: return 2;
+    case KL_T_MATADD: return 8;
+    case KL_T_GEMM_BF16: return 1;
+    case KL_T_TEA: return 4;
+    case KL_T_SAD: return 8;
+    case KL_T_STENCIL: return 4;
+    case KL_T_MRIQ: return 1;
+    default: return 1;
+  }
+}
+
 // One submitted kernel in device memory (128-byte aligned, 256 bytes).
 // Static fields are written by the host before the launch; dynamic fields are
 // zero at launch and owned by the device during the run.

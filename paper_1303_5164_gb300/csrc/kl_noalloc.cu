@@ -39,6 +39,10 @@ constexpr size_t kRunOff = sizeof(TenantDev) * kMaxT;
 constexpr size_t kPhaseOff = (kRunOff + sizeof(RunDev) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kPhaseOff + sizeof(PhaseDev) * kPhaseSlots;
 constexpr int kMaxDevices = 64;
+// the sizes the header documents: 64 x 256 B tenants + the 4,992 B run state
+// (rounded to 5,120 B) + 512 x 144 B phases; the phase ring is a power of two,
+// so 512 slots for the at most 4 x 64 + 16 = 272 phases of a run
+static_assert(kScratchBytes == KL_NOALLOC_SCRATCH_BYTES, "documented size of the device array");
 
 // Device scratch of the allocation-free path (the only storage it uses).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -54,6 +58,7 @@ struct HostImage {
   RunDev run;
   PhaseDev ph0;
 };
+static_assert(sizeof(HostImage) <= 21760, "documented size of the stack image");
 
 }  // namespace
 }  // namespace kl
@@ -100,6 +105,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
     if (rc) return rc;
     if (d.block[0] != KL_BLOCK_THREADS || d.block[1] != 1 || d.block[2] != 1) return KL_EINVAL;
     if (d.grid[0] != sh.grid[0] || d.grid[1] != 1 || d.grid[2] != 1) return KL_EINVAL;
+    if (d.smem_bytes != 0 && d.smem_bytes < sh.smem_bytes) return KL_EINVAL;
     if (sh.total_blocks == 0 || sh.total_blocks >= (1ull << 24)) return KL_EINVAL;
     TenantDev& t = img.t[i];
     t.type = d.type;
@@ -109,7 +115,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
     t.index = i;
     // a slice never exceeds the kernel, and the queue counter (which can
     // overshoot by one slice per CTA when a kernel runs out) stays below 2^32
-    uint64_t sl = d.slice_blocks ? d.slice_blocks : 1u;
+    uint64_t sl = d.slice_blocks ? d.slice_blocks : default_slice(d.type);  // as kl_submit without profiles
     if (sl > t.total) sl = t.total;
     while (sl > 1 && (uint64_t)t.total + sl * ((uint64_t)n_sm * S + 1) >= (1ull << 32)) sl >>= 1;
     t.slice = (uint32_t)sl;
@@ -129,7 +135,8 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
     for (uint32_t b = 0; b < KL_T_COUNT; ++b) {
       R.cp[a][b] = cp_table ? cp_table[a * KL_T_COUNT + b] : 0.0;
       uint32_t sa = slots_a_table ? slots_a_table[a * KL_T_COUNT + b] : S / 2;
-      R.slots_a[a][b] = sa < 1 ? 1 : (sa > S - 1 ? S - 1 : sa);
+      const uint32_t hi = S > 1 ? S - 1 : 1;  // both kernels of a pair keep a slot when S >= 2
+      R.slots_a[a][b] = sa < 1 ? 1 : (sa > hi ? hi : sa);
       R.allowed[a][b] = 1;
     }
   img.ph0.A = -2;

@@ -163,30 +163,6 @@ int validate_args(uint32_t type, const void* a) {
   }
 }
 
-// Pull granularity per type (blocks per slice) when the descriptor leaves it to
-// the runtime; chosen so one atomic covers roughly 16-64 KB of traffic or one
-// long block.
-uint32_t default_slice(uint32_t type) {
-  switch (type) {
-    case KL_T_GATHER: return 4;
-    case KL_T_BLACKSCHOLES: return 8;
-    case KL_T_GEMM_F32: return 1;
-    case KL_T_SPMV_CSR: return 8;
-    case KL_T_PCHASE: return 1;
-    case KL_T_TRIAD: return 2;
-    case KL_T_HIST256: return 2;
-    case KL_T_ESCAPE: return 8;
-    case KL_T_BITONIC: return 2;
-    case KL_T_MATADD: return 8;
-    case KL_T_GEMM_BF16: return 1;
-    case KL_T_TEA: return 4;
-    case KL_T_SAD: return 8;
-    case KL_T_STENCIL: return 4;
-    case KL_T_MRIQ: return 1;
-    default: return 1;
-  }
-}
-
 // Built-in model inputs used until measured profiles are loaded: rough
 // instruction mixes by construction of each tenant body (flagged as such by
 // kl_profile.valid = 2).
@@ -310,6 +286,8 @@ struct kl_runtime {
   ServeDone* sdm_done = nullptr;
   unsigned long long* sdm_cq = nullptr;
   uint32_t s_tail = 0, s_head = 0, s_inflight = 0, s_nstreams = 0;
+  uint32_t s_published = 0;         // kernels [0, s_published) are visible to the device / launched
+  std::vector<TenantDev> s_staged;  // kServeBase: staged descriptors not yet launched, in order
   uint64_t s_footprint = 0;
   std::vector<ServeRec> s_recs;
   std::vector<std::deque<std::pair<uint32_t, cudaEvent_t>>> s_stream_q;  // kServeBase
@@ -634,11 +612,52 @@ uint32_t clamp_slice(const kl_runtime* rt, uint32_t slice, uint32_t total) {
   return (uint32_t)std::max<uint64_t>(sl, 1);
 }
 
+// Serving, plain launches: launch a descriptor on stream seq % nstreams and
+// queue its completion event (lock held).
+int serve_base_launch(kl_runtime* rt, const TenantDev& td) {
+  const uint32_t seq = td.index;
+  const uint32_t k = seq % rt->s_nstreams;
+  cudaEvent_t e = nullptr;
+  if (!rt->s_free_ev.empty()) {
+    e = rt->s_free_ev.back();
+    rt->s_free_ev.pop_back();
+  } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    return KL_ECUDA;
+  }
+  if (native_launch_tenant(td.type, td.args, rt->side[k]) != 0 || cudaEventRecord(e, rt->side[k]) != cudaSuccess) {
+    rt->s_free_ev.push_back(e);
+    return KL_ECUDA;
+  }
+  rt->s_stream_q[k].emplace_back(seq, e);
+  return KL_OK;
+}
+
+// Serving: make every admitted kernel up to s_tail visible (lock held).
+// Co-scheduled: one release store of the new tail into the mapped control
+// word; the device's dispatcher copies the descriptors in and re-plans.
+// Plain launches: launch the staged descriptors in order.
+int serve_flush(kl_runtime* rt) {
+  if (rt->s_published == rt->s_tail) return KL_OK;
+  if (rt->kind == kServe) {
+    __atomic_store_n(&rt->sm_ctl[0], rt->s_tail, __ATOMIC_RELEASE);
+  } else {
+    for (const TenantDev& td : rt->s_staged) {
+      int rc = serve_base_launch(rt, td);
+      if (rc) return rc;
+    }
+    rt->s_staged.clear();
+  }
+  for (uint32_t q = rt->s_published; q < rt->s_tail; ++q) rt->s_recs[q].state = KL_RUNNING;
+  rt->s_published = rt->s_tail;
+  return KL_OK;
+}
+
 // Serving: admit one kernel to the running server (lock held). Co-scheduled:
-// write the descriptor into the mapped ring, then publish the new tail with a
-// release store; the device's dispatcher copies it in and re-plans. Plain
-// launches: launch it now on stream seq % nstreams.
-int serve_publish(kl_runtime* rt, TenantDev td, uint64_t footprint, kl_handle* out) {
+// write the descriptor into the mapped ring; plain launches: keep it in order.
+// With `publish` the kernel (and every one staged before it) becomes visible
+// at once (serve_flush); without, it waits for the next publish, and a
+// serving run that stops first never runs it.
+int serve_publish(kl_runtime* rt, TenantDev td, uint64_t footprint, kl_handle* out, bool publish = true) {
   int p = progress(rt);
   if (p == KL_ECUDA) return KL_ECUDA;
   if (!rt->in_flight || (rt->kind != kServe && rt->kind != kServeBase)) return KL_ESTATE;  // the run has ended
@@ -651,35 +670,21 @@ int serve_publish(kl_runtime* rt, TenantDev td, uint64_t footprint, kl_handle* o
   if (seq >= 0xfffffff0u) return KL_EOVERFLOW;
   td.index = seq;
   td.slice = clamp_slice(rt, td.slice, td.total);
-  if (rt->kind == kServe) {
+  if (rt->kind == kServe)
     memcpy(&rt->sm_ring[seq & (rt->s_ring - 1u)], &td, sizeof(td));
-    __atomic_store_n(&rt->sm_ctl[0], seq + 1u, __ATOMIC_RELEASE);
-  } else {
-    const uint32_t k = seq % rt->s_nstreams;
-    cudaEvent_t e = nullptr;
-    if (!rt->s_free_ev.empty()) {
-      e = rt->s_free_ev.back();
-      rt->s_free_ev.pop_back();
-    } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-      return KL_ECUDA;
-    }
-    if (native_launch_tenant(td.type, td.args, rt->side[k]) != 0 || cudaEventRecord(e, rt->side[k]) != cudaSuccess) {
-      rt->s_free_ev.push_back(e);
-      return KL_ECUDA;
-    }
-    rt->s_stream_q[k].emplace_back(seq, e);
-  }
+  else
+    rt->s_staged.push_back(td);
   ServeRec r{};
   r.t_submit = now_ns();
   r.footprint = footprint;
-  r.state = KL_RUNNING;
+  r.state = KL_PENDING;  // until published
   r.total = td.total;
   rt->s_recs.push_back(r);
   rt->s_tail = seq + 1u;
   rt->s_inflight++;
   rt->s_footprint += footprint;
   *out = make_handle(rt->flight_id, seq);
-  return KL_OK;
+  return publish ? serve_flush(rt) : KL_OK;
 }
 
 }  // namespace
@@ -896,7 +901,7 @@ extern "C" int kl_destroy(kl_runtime* rt) {
   return KL_OK;
 }
 
-extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out) {
+static int submit_impl(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out, bool publish) {
   if (!rt || !d || !out) return KL_EINVAL;
   *out = 0;
   if (d->type >= KL_T_COUNT || !d->args || d->args_size != args_size_of(d->type)) return KL_EINVAL;
@@ -918,7 +923,7 @@ extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out
   td.nstages = sh.nstages;
   td.blocks0 = sh.grid[0];
   memcpy(td.args, d->args, d->args_size);
-  if (rt->serve_on) return serve_publish(rt, td, d->footprint_bytes, out);
+  if (rt->serve_on) return serve_publish(rt, td, d->footprint_bytes, out, publish);
   if (rt->pending.size() >= rt->cap) return KL_EAGAIN;
   if (rt->cfg.mem_cap_bytes && rt->pending_footprint + d->footprint_bytes > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
   Pending p;
@@ -931,6 +936,21 @@ extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out
   rt->pending_footprint += d->footprint_bytes;
   *out = p.handle;
   return KL_OK;
+}
+
+extern "C" int kl_submit(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out) {
+  return submit_impl(rt, d, out, true);
+}
+
+extern "C" int kl_submit_staged(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out) {
+  return submit_impl(rt, d, out, false);
+}
+
+extern "C" int kl_publish(kl_runtime* rt) {
+  if (!rt) return KL_EINVAL;
+  std::lock_guard<std::mutex> lk(rt->mu);
+  if (!rt->serve_on || !rt->in_flight || (rt->kind != kServe && rt->kind != kServeBase)) return KL_OK;
+  return serve_flush(rt);
 }
 
 // Plan and start the pending set; caller holds rt->mu.
@@ -1188,7 +1208,8 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
   rt->in_flight = true;
   rt->flight_id = rt->run_id++;  // kernels still pending keep their handles: they arrive first
   rt->flight_slots = rt->slots;
-  rt->s_tail = rt->s_head = rt->s_inflight = 0;
+  rt->s_tail = rt->s_head = rt->s_inflight = rt->s_published = 0;
+  rt->s_staged.clear();
   rt->s_footprint = 0;
   rt->s_recs.clear();
   rt->completed.clear();

@@ -178,6 +178,8 @@ SIGNATURES = [
     ("kl_tenant_shape_of", C.c_int, [U32, P, U32, C.POINTER(kl_tenant_shape)]),
     ("kl_gemm_bf16_tensor_maps", C.c_int, [C.POINTER(kl_args_gemm_bf16), P]),
     ("kl_submit", C.c_int, [P, C.POINTER(kl_kernel_desc), C.POINTER(U64)]),
+    ("kl_submit_staged", C.c_int, [P, C.POINTER(kl_kernel_desc), C.POINTER(U64)]),
+    ("kl_publish", C.c_int, [P]),
     ("kl_launch", C.c_int, [P]),
     ("kl_serve_start", C.c_int, [P, C.c_int, U32, U64]),
     ("kl_serve_stop", C.c_int, [P, U64]),
@@ -207,6 +209,7 @@ SIGNATURES = [
                                  C.POINTER(I32)]),
 ]
 KL_NOALLOC_MAX_TENANTS = 64
+KL_NOALLOC_SCRATCH_BYTES = 95232
 
 
 def lib_path() -> str:
@@ -331,7 +334,8 @@ class Runtime:
         except Exception:
             pass
 
-    def submit(self, type_: int, args, slice_blocks: int = 0, footprint: int = 0) -> int:
+    def submit(self, type_: int, args, slice_blocks: int = 0, footprint: int = 0, staged: bool = False) -> int:
+        """kl_submit (kl_submit_staged with staged=True)."""
         sh = tenant_shape(type_, args)
         d = kl_kernel_desc()
         d.type = type_
@@ -343,8 +347,12 @@ class Runtime:
         d.args_size = C.sizeof(args)
         d.footprint_bytes = footprint
         h = U64()
-        check(lib().kl_submit(self._h, C.byref(d), C.byref(h)), "kl_submit")
+        fn = lib().kl_submit_staged if staged else lib().kl_submit
+        check(fn(self._h, C.byref(d), C.byref(h)), "kl_submit_staged" if staged else "kl_submit")
         return h.value
+
+    def publish(self):
+        check(lib().kl_publish(self._h), "kl_publish")
 
     def submit_desc(self, desc: kl_kernel_desc) -> int:
         h = U64()

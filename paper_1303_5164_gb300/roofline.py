@@ -78,6 +78,56 @@ def fp32_flops(name: str, inp: dict, escape_iters: int | None = None) -> int:
     return 0
 
 
+# lane operations (one issue slot of one of the SM's 128 lanes) per unit of work
+ESCAPE_OPS_PER_ITER = 9          # x*x, y*y, x2+y2, compare, 2*x, *y, +cy, x2-y2, +cx
+BITONIC_OPS_PER_EXCHANGE = 2     # min and max of the pair
+
+
+def lane_ops(name: str, inp: dict, escape_iters: int | None = None) -> int:
+    """Issue slots of the written definition, counted per lane: each binary32
+    operation (a fused multiply-add once), integer min/max, shared-memory
+    atomic, or load of a dependent chain takes one slot of one of the 128
+    lanes of an SM. Set against numSM x 128 x f_SM slots per second this is
+    the issue-bound time of tenants that are neither HBM- nor FFMA-bound
+    (Black-Scholes, escape-time, the bitonic passes, TEA)."""
+    if name == "gemm_f32":
+        return inp["M"] * inp["N"] * inp["K"]
+    if name == "blackscholes":
+        return BS_FLOPS_PER_OPTION * inp["n"]
+    if name == "spmv_csr":
+        return inp["nnz"]
+    if name == "triad":
+        return inp["n"]
+    if name == "escape":
+        return ESCAPE_OPS_PER_ITER * int(escape_iters or 0)
+    if name == "bitonic":
+        L = inp["log2n"]
+        return BITONIC_OPS_PER_EXCHANGE * (inp["n"] // 2) * (L * (L + 1) // 2)
+    if name == "hist256":
+        return inp["n"]
+    if name == "pchase":
+        return inp["hops"] * inp["nchasers"]
+    if name == "gather":
+        return inp["n"]
+    if name == "matadd":
+        return inp["n"] * inp["n"]
+    if name == "tea":
+        return 32 * 10 * inp["n"]      # 32 cycles of two 5-operation Feistel rounds
+    if name == "stencil":
+        return 8 * inp["nx"] * inp["ny"] * inp["nz"]
+    if name == "mriq":
+        return 30 * inp["numK"] * inp["numX"]
+    if name == "sad":
+        D = 2 * inp["range"] + 1
+        return 3 * 16 * (inp["width"] // 4) * (inp["height"] // 4) * D * D  # sub, abs, add per pixel
+    return 0
+
+
+def lane_peak(n_sm: int, f_sm_hz: float) -> float:
+    """Issue slots per second: 4 schedulers x 32 lanes per SM per cycle."""
+    return n_sm * 128 * f_sm_hz
+
+
 def fp32_peak_flops(n_sm: int, f_sm_hz: float) -> float:
     """FFMA peak: 128 binary32 lanes per SM, 2 operations per fused multiply-add."""
     return n_sm * 128 * 2 * f_sm_hz

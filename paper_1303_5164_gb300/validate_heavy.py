@@ -8,7 +8,8 @@ balanced slot split (Eq. executiontime), then all four submitted together.
 Per run: kernel time, and per phase the measured IPC of each kernel (blocks
 finished x instructions per block over the phase's cycles on all SMs) beside
 the Markov model's prediction (Section 4.4). The four-kernel run is also timed
-as plain launches on 4 streams and on one stream.
+as plain launches on 4 streams and on one stream. Every run's outputs are
+compared bit for bit with each kernel's plain launch.
 
     python -m paper_1303_5164_gb300.validate_heavy --out heavy.json
 """
@@ -32,34 +33,77 @@ HEAVY = {
 }
 
 
-def run(out_path, reps=3):
-    import torch
+def heavy_inputs():
+    """Seeded inputs of the four kernels (config seed 5, tenant indices 40..43)."""
     from workloads import gen
-    from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
-    from paper_1303_5164_gb300.validate_pairs import _profiles, _phase_ipc
-    build.build()
+    return {nm: gen.gen_tenant(nm, 5, 40 + i, **HEAVY[nm]) for i, nm in enumerate(HEAVY)}
+
+
+def heavy_setup(K):
+    """Runtime configuration, model parameters and profiles of every run here:
+    4 slots per SM, the measured profiles and latency fit."""
+    from paper_1303_5164_gb300.validate_pairs import _profiles
     profs, doc = _profiles(K)
     cfg = K.config_default()
     cfg.slots_per_sm = 4
     rt = K.Runtime(cfg)
     mp = rt.model_params()
+    rt.close()
     mp.a0, mp.b0 = doc.get("a0", 1.0), doc.get("b0", 0.0)
     mp.dram_bytes_per_s = doc.get("dram_bytes_per_s", mp.dram_bytes_per_s)
+    return cfg, mp, profs
+
+
+def heavy_runtime(K, cfg, mp, profs):
+    rt = K.Runtime(cfg)
     rt.set_model_params(mp)
     rt.set_profiles(profs)
-    S = rt.run_stats().slots_per_sm
-    rt.close()
+    return rt
+
+
+def run(out_path, reps=3):
+    import numpy as np
+    import torch
+    from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
+    from paper_1303_5164_gb300.validate_pairs import _phase_ipc
+    build.build()
+    cfg, mp, profs = heavy_setup(K)
+    S = cfg.slots_per_sm
     names = list(HEAVY)
-    tens = {nm: T.make(nm, gen.gen_tenant(nm, 5, 40 + i, **HEAVY[nm])) for i, nm in enumerate(names)}
+    inputs = heavy_inputs()
+    tens = {nm: T.make(nm, inputs[nm]) for nm in names}
     torch.cuda.synchronize()
     res = {"slots_per_sm": S, "sizes": HEAVY, "solo": {}, "pairs": {}}
 
+    def poison(sel):
+        for nm in sel:
+            for k in tens[nm].outputs:
+                tens[nm].bufs[k].fill_(-1)
+
+    # each kernel's output as one plain launch: every co-scheduled run below
+    # must reproduce it bit for bit
+    ref = {}
+    r0 = heavy_runtime(K, cfg, mp, profs)
+    for nm in names:
+        poison([nm])
+        r0.submit(tens[nm].type, tens[nm].args)
+        r0.launch_baseline(K.KL_BASE_SERIAL, 1)
+        assert r0.drain() == 0
+        ref[nm] = tens[nm].fetch()
+    r0.close()
+
+    def check(sel):
+        for nm in sel:
+            got = tens[nm].fetch()
+            for k, v in ref[nm].items():
+                if got[k].tobytes() != v.tobytes():
+                    raise AssertionError(f"{nm}.{k}: co-scheduled output differs from the plain launch")
+
     def go(sel, base=None, ns=4):
-        r2 = K.Runtime(cfg)
-        r2.set_model_params(mp)
-        r2.set_profiles(profs)
+        r2 = heavy_runtime(K, cfg, mp, profs)
         best = None
         for _ in range(reps):
+            poison(sel)
             for nm in sel:
                 r2.submit(tens[nm].type, tens[nm].args)
             if base is None:
@@ -67,6 +111,7 @@ def run(out_path, reps=3):
             else:
                 r2.launch_baseline(base, ns)
             assert r2.drain() == 0
+            check(sel)
             ker = r2.run_stats().kernel_ns / 1e3
             if best is None or ker < best[1]:
                 best = (r2.phases() if base is None else [], ker)

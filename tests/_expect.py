@@ -49,6 +49,21 @@ def expected(name: str, inp: dict) -> dict:
     raise ValueError(name)
 
 
+LARGE_GEMM_FLOPS = 1 << 28   # FP32 GEMMs above this go through check_gemm_f32_large
+
+
+def expected_for_job(job):
+    """Worker of a process pool: the oracle's outputs for one job
+    (name, config seed, tenant index, size), regenerating its seeded inputs;
+    None for FP32 GEMMs above LARGE_GEMM_FLOPS (checked in the parent)."""
+    from workloads import gen
+    name, cs, ti, size = job
+    if name == "gemm_f32" and 2 * size["M"] * size["N"] * size["K"] > LARGE_GEMM_FLOPS:
+        return None
+    OT.build()
+    return expected(name, gen.gen_tenant(name, cs, ti, **size))
+
+
 def gemm_bf16_bound(K, cabs):
     """|C_gpu - C_exact| <= K * 2^-23 * sum_k |a b|: the products of bfloat16
     values are exact in binary32, and each of the at most K binary32 additions
@@ -80,6 +95,28 @@ def same_bits(a, b) -> bool:
         return np.array_equal(a.view(np.uint32 if a.itemsize == 4 else np.uint64),
                               b.astype(a.dtype).view(np.uint32 if a.itemsize == 4 else np.uint64))
     return np.array_equal(a, b.astype(a.dtype) if a.dtype != b.dtype else b)
+
+
+def check_gemm_f32_large(inp: dict, got_C, n_samples: int = 256, seed: int = 0):
+    """An FP32 GEMM too large for the chain oracle's loop: every entry within
+    K 2^-24 sum|ab| of the binary64 value of the definition, and sampled
+    entries (every tile corner of the first and last tile rows and columns,
+    plus random ones) bit for bit against the chain oracle."""
+    A, B = inp["A"], inp["B"]
+    M, K = A.shape
+    N = B.shape[1]
+    c = np.asarray(got_C, dtype=np.float32).reshape(M, N)
+    c64, cabs = OT.gemm_f32_exact(A, B)
+    err = np.abs(c.astype(np.float64) - c64)
+    bad = np.argwhere(err > K * U * cabs)
+    assert len(bad) == 0, f"gemm_f32 entries over the chain bound: {bad[:5].tolist()}"
+    rng = np.random.default_rng(seed)
+    ii = [0, M - 1, min(63, M - 1), min(64, M - 1), M - 1]
+    jj = [0, N - 1, min(63, N - 1), min(64, N - 1), 0]
+    ii = np.concatenate([ii, rng.integers(0, M, n_samples)]).astype(np.int64)
+    jj = np.concatenate([jj, rng.integers(0, N, n_samples)]).astype(np.int64)
+    want = OT.gemm_f32_sample(A, B, ii, jj)
+    assert same_bits(c[ii, jj], want), "gemm_f32 sampled entries differ from the chain oracle"
 
 
 def check(name: str, inp: dict, got: dict, exp: dict):

@@ -98,6 +98,25 @@ def test_gemm_identity_integer_and_error_bound(oracle_tenants):
     assert np.array_equal(oracle_tenants.gemm_f32_sample(d["A"], d["B"], ii, jj), C[ii, jj])
 
 
+def test_gemm_exact_value_and_chain_bound(oracle_tenants):
+    rng = np.random.default_rng(3)
+    Ai = rng.integers(-50, 51, (45, 130)).astype(np.float32)
+    Bi = rng.integers(-50, 51, (130, 27)).astype(np.float32)
+    c64, cabs = oracle_tenants.gemm_f32_exact(Ai, Bi)
+    assert np.array_equal(c64, (Ai.astype(np.int64) @ Bi.astype(np.int64)).astype(np.float64))
+    assert np.array_equal(cabs, (np.abs(Ai).astype(np.int64) @ np.abs(Bi).astype(np.int64)).astype(np.float64))
+    # the chain oracle lies within K 2^-24 sum|ab| of the exact value, and the
+    # bound is tight enough that a wrong operand (B's rows reversed) fails it
+    # almost everywhere
+    d = gen.gen_gemm_f32(2, 1, 96, 96, 257)
+    C = oracle_tenants.gemm_f32(d["A"], d["B"])
+    c64, cabs = oracle_tenants.gemm_f32_exact(d["A"], d["B"])
+    bound = 257 * 2.0 ** -24 * cabs
+    assert np.all(np.abs(C - c64) <= bound)
+    wrong, _ = oracle_tenants.gemm_f32_exact(d["A"], d["B"][::-1].copy())
+    assert np.mean(np.abs(wrong - c64) > bound) > 0.99
+
+
 def test_spmv_small_integers_exact_and_bound(oracle_tenants):
     d = gen.gen_spmv_csr(2, 0, 3000)
     rowptr, col = d["rowptr"], d["col"]
