@@ -466,6 +466,132 @@ def make_runtime(K, device: int = 0, stream: int = 0, flags=None, profiles: str 
     return rt, mp_, model_info
 
 
+def e2e_leg(K, T, rt, tens, names, inputs, stream, local, world, steps, barrier):
+    """The metric end to end through the public API from pinned host memory.
+    Every step uploads its 64 kernels' inputs, runs them (kl_submit x 64,
+    kl_launch, kl_drain) and downloads every output. Two device buffer sets
+    (step k uses set k % 2) let the upload of step k+1 and the download of
+    step k-1 run on their own streams while step k computes; all of every
+    step's copies are inside the timed region. Returns the e2e dict, with the
+    per-step upload, compute and download times (CUDA events, medians)."""
+    import torch
+    n = len(tens)
+    sets = [tens, [T.make(nm, x) for nm, x in zip(names, inputs)]]
+    affinity = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
+    numa_node, numa_cores = bind_host_to_gpu_node(local)
+    pin_in, pin_out = [], []
+    h2d = d2h = 0
+    for t in tens:
+        ins = {k: v.cpu().pin_memory() for k, v in t.bufs.items() if k not in t.outputs}
+        outs = {k: torch.empty(t.bufs[k].shape, dtype=t.bufs[k].dtype, pin_memory=True) for k in t.outputs}
+        h2d += sum(v.numel() * v.element_size() for v in ins.values())
+        d2h += sum(v.numel() * v.element_size() for v in outs.values())
+        pin_in.append(ins)
+        pin_out.append(outs)
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def tev():
+        return torch.cuda.Event(enable_timing=True)
+
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]     # inputs of set b uploaded
+    ev_done = [torch.cuda.Event(), torch.cuda.Event()]   # compute on set b finished
+    ev_out = [torch.cuda.Event(), torch.cuda.Event()]    # outputs of set b downloaded
+    spans = {"upload": [], "compute": [], "download": []}
+
+    def upload(b):
+        s_in.wait_event(ev_done[b])          # the previous run on set b no longer reads its inputs
+        e0, e1 = tev(), tev()
+        e0.record(s_in)
+        with torch.cuda.stream(s_in):
+            for t, ins in zip(sets[b], pin_in):
+                for k, v in ins.items():
+                    t.bufs[k].copy_(v, non_blocking=True)
+        e1.record(s_in)
+        ev_in[b].record(s_in)
+        spans["upload"].append((e0, e1))
+
+    def download(b):
+        s_out.wait_event(ev_done[b])
+        e0, e1 = tev(), tev()
+        e0.record(s_out)
+        with torch.cuda.stream(s_out):
+            for t, outs in zip(sets[b], pin_out):
+                for k, v in outs.items():
+                    v.copy_(t.bufs[k], non_blocking=True)
+        e1.record(s_out)
+        ev_out[b].record(s_out)
+        spans["download"].append((e0, e1))
+
+    def run(nsteps):
+        for v in spans.values():
+            v.clear()
+        barrier()
+        e0, e1 = tev(), tev()
+        e0.record(stream)
+        s_in.wait_event(e0)
+        s_out.wait_event(e0)
+        upload(0)
+        for k in range(nsteps):
+            b = k % 2
+            if k + 1 < nsteps:
+                upload(1 - b)
+            stream.wait_event(ev_in[b])
+            stream.wait_event(ev_out[b])     # outputs of set b read back before they are overwritten
+            c0, c1 = tev(), tev()
+            c0.record(stream)
+            for t in sets[b]:
+                rt.submit(t.type, t.args)
+            rt.launch()
+            rc = rt.drain()
+            if rc != 0:
+                raise RuntimeError(f"co-scheduled run failed: {K.lib().kl_strerror(rc).decode()}")
+            c1.record(stream)
+            spans["compute"].append((c0, c1))
+            ev_done[b].record(stream)
+            download(b)
+        for b in range(min(2, nsteps)):
+            stream.wait_event(ev_out[b])
+        e1.record(stream)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / nsteps, world, "cuda")
+
+    run(2)
+    ms = run(steps)
+    per = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in spans.items() if v}
+
+    def copy_gbs(upload_dir):
+        # one step's copies alone, on one stream: the link's achieved rate
+        q = torch.cuda.Stream()
+        c0, c1 = tev(), tev()
+        torch.cuda.synchronize()
+        c0.record(q)
+        with torch.cuda.stream(q):
+            for t, ins, outs in zip(tens, pin_in, pin_out):
+                if upload_dir:
+                    for k, v in ins.items():
+                        t.bufs[k].copy_(v, non_blocking=True)
+                else:
+                    for k, v in outs.items():
+                        v.copy_(t.bufs[k], non_blocking=True)
+        c1.record(q)
+        c1.synchronize()
+        return (h2d if upload_dir else d2h) / (c0.elapsed_time(c1) / 1e3) / 1e9
+
+    h2d_gbs, d2h_gbs = copy_gbs(True), copy_gbs(False)
+    if affinity is not None:
+        os.sched_setaffinity(0, affinity)
+    return {"value": job_value(n, world, ms), "unit": "kernels/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms,
+            "step_ms_median": {k: round(v, 3) for k, v in per.items()},
+            "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs,
+            "host_numa_node": numa_node, "host_cores_bound": numa_cores,
+            "how": "public API (kl_submit/kl_launch/kl_drain) on pinned host buffers; uploads and downloads on "
+                   "their own streams, overlapping the neighbouring steps' compute (two device buffer sets); "
+                   "pinned buffers allocated with the process bound to the GPU's NUMA node (when sysfs "
+                   "names one); step_ms_median = each stream's span per step; *_gbs_alone = one step's copies "
+                   "in one direction, alone on one stream"}
+
+
 # ---------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -617,104 +743,7 @@ def run_ours(args):
     # end to end through the public API with host buffers: H2D inputs, run, D2H outputs
     e2e = None
     if not args.no_e2e:
-        # End to end through the public API from pinned host memory, pipelined
-        # over two device buffer sets (step k uses set k % 2): the upload of
-        # step k+1's inputs and the download of step k-1's outputs run on their
-        # own streams while step k computes. Every step's copies are inside
-        # the timed region.
-        sets = [tens, [T.make(nm, x) for nm, x in zip(names, inputs)]]
-        affinity = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
-        numa_node, numa_cores = bind_host_to_gpu_node(local)
-        pin_in, pin_out = [], []
-        h2d = d2h = 0
-        for t in tens:
-            ins = {k: v.cpu().pin_memory() for k, v in t.bufs.items() if k not in t.outputs}
-            outs = {k: torch.empty(t.bufs[k].shape, dtype=t.bufs[k].dtype, pin_memory=True) for k in t.outputs}
-            h2d += sum(v.numel() * v.element_size() for v in ins.values())
-            d2h += sum(v.numel() * v.element_size() for v in outs.values())
-            pin_in.append(ins)
-            pin_out.append(outs)
-        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event(), torch.cuda.Event()]     # inputs of set b uploaded
-        ev_done = [torch.cuda.Event(), torch.cuda.Event()]   # compute on set b finished
-        ev_out = [torch.cuda.Event(), torch.cuda.Event()]    # outputs of set b downloaded
-
-        def upload(b):
-            s_in.wait_event(ev_done[b])          # the previous run on set b no longer reads its inputs
-            with torch.cuda.stream(s_in):
-                for t, ins in zip(sets[b], pin_in):
-                    for k, v in ins.items():
-                        t.bufs[k].copy_(v, non_blocking=True)
-            ev_in[b].record(s_in)
-
-        def download(b):
-            s_out.wait_event(ev_done[b])
-            with torch.cuda.stream(s_out):
-                for t, outs in zip(sets[b], pin_out):
-                    for k, v in outs.items():
-                        v.copy_(t.bufs[k], non_blocking=True)
-            ev_out[b].record(s_out)
-
-        def e2e_run(steps):
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s_in.wait_event(e0)
-            s_out.wait_event(e0)
-            upload(0)
-            for k in range(steps):
-                b = k % 2
-                if k + 1 < steps:
-                    upload(1 - b)
-                stream.wait_event(ev_in[b])
-                stream.wait_event(ev_out[b])     # outputs of set b read back before they are overwritten
-                for t in sets[b]:
-                    rt.submit(t.type, t.args)
-                rt.launch()
-                rc = rt.drain()
-                if rc != 0:
-                    raise RuntimeError(f"co-scheduled run failed: {K.lib().kl_strerror(rc).decode()}")
-                ev_done[b].record(stream)
-                download(b)
-            for b in range(min(2, steps)):
-                stream.wait_event(ev_out[b])
-            e1.record(stream)
-            barrier()
-            return max_over_ranks(e0.elapsed_time(e1) / steps, world, "cuda")
-
-        e2e_run(2)
-        ms_e2e = e2e_run(max(4, args.steps))
-
-        def copy_gbs(upload_dir):
-            # one step's copies alone, on one stream: the link's achieved rate
-            q = torch.cuda.Stream()
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            c0.record(q)
-            with torch.cuda.stream(q):
-                for t, ins, outs in zip(tens, pin_in, pin_out):
-                    if upload_dir:
-                        for k, v in ins.items():
-                            t.bufs[k].copy_(v, non_blocking=True)
-                    else:
-                        for k, v in outs.items():
-                            v.copy_(t.bufs[k], non_blocking=True)
-            c1.record(q)
-            c1.synchronize()
-            return (h2d if upload_dir else d2h) / (c0.elapsed_time(c1) / 1e3) / 1e9
-
-        h2d_gbs, d2h_gbs = copy_gbs(True), copy_gbs(False)
-        e2e = {"value": job_value(n, world, ms_e2e), "unit": "kernels/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
-               "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs,
-               "host_numa_node": numa_node, "host_cores_bound": numa_cores,
-               "how": "public API (kl_submit/kl_launch/kl_drain) on pinned host buffers; uploads and downloads on "
-                      "their own streams, overlapping the neighbouring steps' compute (two device buffer sets); "
-                      "pinned buffers allocated with the process bound to the GPU's NUMA node (when sysfs "
-                      "names one); *_gbs_alone = one step's copies in one direction, alone on one stream"}
-        del sets, pin_in, pin_out
-        if affinity is not None:
-            os.sched_setaffinity(0, affinity)
+        e2e = e2e_leg(K, T, rt, tens, names, inputs, stream, local, world, max(4, args.steps), barrier)
         torch.cuda.empty_cache()
 
     cpu = None

@@ -27,6 +27,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "kl_internal.h"
 #include "tenants.cuh"
 
@@ -846,6 +848,46 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
     atomicAdd(&R->plan_ns, ctl.acc_plan);
     atomicAdd(&R->ctas_done, 1u);
   }
+}
+
+// Run staging through the SMs: copies between the runtime's pinned host image
+// (device-accessible) and its device queue, so that a launch never waits
+// behind the caller's bulk transfers queued on the copy engines.
+struct CopyList {
+  CopySeg seg[4];
+  uint32_t n;
+};
+
+__global__ void __launch_bounds__(kThreads) stage_copy_kernel(CopyList L) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nth = (size_t)gridDim.x * blockDim.x;
+  for (uint32_t k = 0; k < L.n && k < 4u; ++k) {
+    const CopySeg sg = L.seg[k];
+    if ((((uintptr_t)sg.dst | (uintptr_t)sg.src | sg.bytes) & 15u) == 0) {
+      uint4* d = static_cast<uint4*>(sg.dst);
+      const uint4* s = static_cast<const uint4*>(sg.src);
+      for (size_t i = tid; i < sg.bytes / 16u; i += nth) d[i] = s[i];
+    } else {
+      unsigned char* d = static_cast<unsigned char*>(sg.dst);
+      const unsigned char* s = static_cast<const unsigned char*>(sg.src);
+      for (size_t i = tid; i < sg.bytes; i += nth) d[i] = s[i];
+    }
+  }
+}
+
+// dst/src pairs (device-accessible pointers) copied by one kernel on stream s
+int stage_copy(const CopySeg* segs, uint32_t n, cudaStream_t s) {
+  if (n == 0 || n > 4) return -1;
+  CopyList L{};
+  size_t total = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    L.seg[k] = segs[k];
+    total += segs[k].bytes;
+  }
+  L.n = n;
+  const uint32_t blocks = (uint32_t)std::min<size_t>(64, std::max<size_t>(1, total / (16u * kThreads * 4u)));
+  stage_copy_kernel<<<blocks, kThreads, 0, s>>>(L);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // ------------------------------------------------------------------ host side

@@ -138,4 +138,12 @@ struct alignas(128) RunDev {
   alignas(128) uint32_t sm_ticket[kMaxSM];
 };
 
+// One device-side copy (kl_cosched.cu, stage_copy): dst and src are
+// device-accessible pointers (device memory or pinned host memory).
+struct CopySeg {
+  void* dst;
+  const void* src;
+  unsigned long long bytes;
+};
+
 }  // namespace kl

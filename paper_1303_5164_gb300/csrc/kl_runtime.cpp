@@ -32,6 +32,7 @@ int cosched_occupancy(int* ctas_per_sm, int build);
 int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
                    int build, cudaStream_t stream);
 int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s);
+int stage_copy(const CopySeg* segs, uint32_t n, cudaStream_t s);
 namespace model {
 int pair(const kl_model_params& g, const kl_profile& pa, const kl_profile& pb, uint32_t slots, int states,
          uint32_t policy, uint32_t fixed_a, double* cA, double* cB, double* cpv, double* dT, double* solo,
@@ -241,6 +242,9 @@ struct kl_runtime {
   TenantDev* h_tenants = nullptr;
   RunDev* h_run = nullptr;
   PhaseDev* h_phases = nullptr;
+  TenantDev* hd_tenants = nullptr;  // device addresses of the three pinned buffers above
+  RunDev* hd_run = nullptr;
+  PhaseDev* hd_phases = nullptr;
   std::vector<Pending> pending;
   uint64_t pending_footprint = 0;
   uint64_t run_id = 1;       // id of the run the pending set will become
@@ -832,6 +836,11 @@ extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime*
   if (cudaMallocHost(&rt->h_tenants, sizeof(TenantDev) * rt->ring_slots) != cudaSuccess) goto fail_mem;
   if (cudaMallocHost(&rt->h_run, sizeof(RunDev)) != cudaSuccess) goto fail_mem;
   if (cudaMallocHost(&rt->h_phases, sizeof(PhaseDev) * rt->phase_slots) != cudaSuccess) goto fail_mem;
+  // device addresses of the pinned image (the SM-side staging copies use them)
+  if (cudaHostGetDevicePointer((void**)&rt->hd_tenants, rt->h_tenants, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&rt->hd_run, rt->h_run, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&rt->hd_phases, rt->h_phases, 0) != cudaSuccess)
+    goto fail_cuda;
   if (cudaEventCreate(&rt->ev_start) != cudaSuccess || cudaEventCreate(&rt->ev_done) != cudaSuccess ||
       cudaEventCreate(&rt->ev_k0) != cudaSuccess || cudaEventCreate(&rt->ev_k1) != cudaSuccess ||
       cudaEventCreateWithFlags(&rt->ev_fork, cudaEventDisableTiming) != cudaSuccess)
@@ -1003,18 +1012,22 @@ static int launch_locked(kl_runtime* rt) {
   first.chain[0] = first.chain[1] = -1;
   rt->h_phases[0] = first;
   cudaStream_t s = rt->stream;
+  // the run's image goes in and its results come out through the SMs (the
+  // pinned host image is device-accessible), not the copy engines: a caller's
+  // bulk transfers queued on those engines must not delay the launch
+  const CopySeg in[3] = {{rt->d_tenants, rt->hd_tenants, sizeof(TenantDev) * n},
+                         {rt->d_run, rt->hd_run, sizeof(RunDev)},
+                         {rt->d_phases, rt->hd_phases, sizeof(PhaseDev)}};
+  const CopySeg out[3] = {{rt->hd_tenants, rt->d_tenants, sizeof(TenantDev) * n},
+                          {rt->hd_run, rt->d_run, sizeof(RunDev)},
+                          {rt->hd_phases, rt->d_phases, sizeof(PhaseDev) * R.max_phases}};
   rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
-  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_tenants, rt->h_tenants, sizeof(TenantDev) * n, cudaMemcpyHostToDevice, s));
-  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_run, rt->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, s));
-  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->d_phases, rt->h_phases, sizeof(PhaseDev), cudaMemcpyHostToDevice, s));
+  if (!rc && stage_copy(in, 3, s) != 0) rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
   if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, S, smem, build, s) != 0)
     rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
-  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_tenants, rt->d_tenants, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s));
-  if (!rc) rc = cuda_ok(cudaMemcpyAsync(rt->h_run, rt->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
-  if (!rc)
-    rc = cuda_ok(cudaMemcpyAsync(rt->h_phases, rt->d_phases, sizeof(PhaseDev) * R.max_phases, cudaMemcpyDeviceToHost, s));
+  if (!rc && stage_copy(out, 3, s) != 0) rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_done, s));
   if (rc) return rc;
   rt->flight.swap(rt->pending);

@@ -64,10 +64,10 @@ constexpr int kMriqPerBlock = 256;       // k-samples (stage 0) or image points 
 __host__ __device__ inline uint32_t bitonic_tile_log2(uint32_t L) {
   return L < (uint32_t)kBitonicTileLog2 ? L : (uint32_t)kBitonicTileLog2;
 }
-constexpr uint32_t kBitonicFuse = 4;   // merge levels per global pass (16 keys per thread)
+constexpr uint32_t kBitonicHigh = 10;  // distances above the tile handled by one pass
 __host__ __device__ inline uint32_t bitonic_nstages(uint32_t L) {
   uint32_t P = bitonic_tile_log2(L), n = 1;
-  for (uint32_t d = 1; d + P <= L; ++d) n += (d + kBitonicFuse - 1) / kBitonicFuse + 1;
+  for (uint32_t d = 1; d + P <= L; ++d) n += (d + kBitonicHigh - 1) / kBitonicHigh + 1;
   return n;
 }
 
@@ -541,6 +541,9 @@ __device__ __forceinline__ void spmv_csr_block(const kl_args_spmv_csr& a, uint32
 __device__ __forceinline__ void pchase_block(const kl_args_pchase& a, uint32_t vb) {
   // one chain per thread: the chains of a kernel spread over every SM, whose
   // outstanding-miss capacity bounds how many dependent loads are in flight
+  // (four chains per thread, 1024 chasers per block, was measured slower on
+  // GB300: a kernel's blocks then cover fewer SMs, and concurrent chase
+  // kernels thrash the address translation caches sooner)
   const uint32_t t = vb * kChasersPerBlock + threadIdx.x;
   if (t >= a.nchasers) return;
   int p = __ldg(a.start + t);
@@ -652,18 +655,20 @@ __device__ __forceinline__ void escape_block(const kl_args_escape& a, uint32_t v
 // compare distance j = 2^jl; a compare-exchange (i, i+j) orders ascending iff
 // (i & k) == 0 (the standard bitonic network on global indices). Stages:
 //   0                 : sort every tile in shared memory (lv = 1..P), in -> out
-//   for lv = P+1 .. L : global passes over the levels jl = lv-1 .. P, up to 4
-//                       levels per pass: each thread holds a group of 2^m keys
-//                       spaced 2^jlo apart in registers and runs the m levels
-//                       there; then one shared-memory stage for jl = P-1 .. 0,
-//                       two levels per barrier.
+//   for lv = P+1 .. L : the distances above the tile, jl = lv-1 .. P, in passes
+//                       of up to 10 levels: a block gathers the 4096 keys whose
+//                       indices differ only in those m distance bits and in
+//                       the 12 - m lowest bits (runs of at least 4 contiguous
+//                       keys), runs the m levels in shared memory and writes
+//                       them back; then one pass for jl = P-1 .. 0 on
+//                       contiguous 4096-key tiles.
 // Every stage has 2^(L-P) blocks of 4096 (or 2^L) keys.
 
 struct BitonicStep {
-  uint32_t kind;   // 0 tile sort, 1 global fused pass, 2 tile merge
+  uint32_t kind;   // 0 tile sort, 1 pass over distances above the tile, 2 tile merge
   uint32_t lv;     // log2 k
-  uint32_t jhi;    // global pass: highest level
-  uint32_t jlo;    // global pass: lowest level
+  uint32_t jhi;    // kind 1: highest level
+  uint32_t jlo;    // kind 1: lowest level
 };
 
 __host__ __device__ inline BitonicStep bitonic_step(uint32_t L, uint32_t s) {
@@ -671,10 +676,10 @@ __host__ __device__ inline BitonicStep bitonic_step(uint32_t L, uint32_t s) {
   if (s == 0) return BitonicStep{0, P, 0, 0};
   s -= 1;
   for (uint32_t lv = P + 1; lv <= L; ++lv) {
-    const uint32_t d = lv - P, npass = (d + kBitonicFuse - 1) / kBitonicFuse;
+    const uint32_t d = lv - P, npass = (d + kBitonicHigh - 1) / kBitonicHigh;
     if (s < npass) {
-      const uint32_t jhi = lv - 1 - kBitonicFuse * s;
-      const uint32_t jlo = jhi + 1 >= P + kBitonicFuse ? jhi + 1 - kBitonicFuse : P;
+      const uint32_t jhi = lv - 1 - kBitonicHigh * s;
+      const uint32_t jlo = jhi + 1 >= P + kBitonicHigh ? jhi + 1 - kBitonicHigh : P;
       return BitonicStep{1, lv, jhi, jlo};
     }
     s -= npass;
@@ -688,38 +693,6 @@ __device__ __forceinline__ void cmpx(uint32_t& x, uint32_t& y, bool asc) {
   uint32_t lo = min(x, y), hi = max(x, y);
   x = asc ? lo : hi;
   y = asc ? hi : lo;
-}
-
-// One global pass over M levels (jlo .. jlo+M-1) for a 4096-key block. All 16
-// keys of the thread are loaded before any is stored.
-template <int M>
-__device__ __forceinline__ void bitonic_fused(uint32_t* out, uint32_t vb, uint32_t lv, uint32_t jlo) {
-  constexpr int G = 1 << M;                 // keys per group
-  constexpr int PER_THREAD = 16 / G;        // groups per thread (16 keys per thread)
-  const uint32_t k = 1u << lv;              // keys < 2^30: 32-bit indices throughout
-  const uint32_t s = 1u << jlo;
-  uint32_t base[PER_THREAD];
-  uint32_t v[16];
-#pragma unroll
-  for (int u = 0; u < PER_THREAD; ++u) {
-    const uint32_t q = vb * (4096u / G) + (uint32_t)u * 256u + threadIdx.x;
-    base[u] = ((q >> jlo) << (jlo + M)) | (q & (s - 1));
-#pragma unroll
-    for (int r = 0; r < G; ++r) v[u * G + r] = __ldcg(out + base[u] + r * s);
-  }
-#pragma unroll
-  for (int u = 0; u < PER_THREAD; ++u) {
-    const bool asc = (base[u] & k) == 0;
-#pragma unroll
-    for (int lvl = M - 1; lvl >= 0; --lvl)
-#pragma unroll
-      for (int r = 0; r < G; ++r)
-        if (!(r & (1 << lvl))) cmpx(v[u * G + r], v[u * G + r + (1 << lvl)], asc);
-  }
-#pragma unroll
-  for (int u = 0; u < PER_THREAD; ++u)
-#pragma unroll
-    for (int r = 0; r < G; ++r) out[base[u] + r * s] = v[u * G + r];
 }
 
 // shared-memory tile index with one padding word per 32 (power-of-two strides
@@ -850,6 +823,60 @@ __device__ __forceinline__ void bitonic_tile_merge_regs(uint32_t* out, uint32_t*
   for (int q = 0; q < 4; ++q) o[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+// The same levels restricted to register bits >= blo (the others are not
+// distances of this pass).
+template <bool ASC>
+__device__ __forceinline__ void bt_levels_dir_from(uint32_t (&v)[16], int blo) {
+#pragma unroll
+  for (int b = 3; b >= 0; --b) {
+    if (b < blo) continue;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      if (r & (1 << b)) continue;
+      uint32_t lo = min(v[r], v[r | (1 << b)]), hi = max(v[r], v[r | (1 << b)]);
+      v[r] = ASC ? lo : hi;
+      v[r | (1 << b)] = ASC ? hi : lo;
+    }
+  }
+}
+
+// Distances 2^jhi .. 2^jlo (all >= 4096, m = jhi - jlo + 1 <= 10 of them) at
+// merge size 2^lv for block vb. Tile position i of the block's 4096 keys has
+// bits [0, 12 - m) = the low bits of the global index (a contiguous run of
+// 2^(12-m) >= 4 keys) and bits [12 - m, 12) = the distance bits jlo .. jhi;
+// the block number supplies the global bits between 12 - m and jlo and those
+// above jhi. Bit lv is above jhi, so the direction is the same for the whole
+// block. The three register patterns of the tile merge carry tile bits 11..8,
+// 7..4 and 3..0; levels whose tile bit is below 12 - m are skipped.
+__device__ __forceinline__ void bitonic_high_pass(uint32_t* out, uint32_t* t, uint32_t vb, uint32_t lv, uint32_t jhi,
+                                                  uint32_t jlo) {
+  const uint32_t m = jhi - jlo + 1, lowb = 12u - m, ab = jlo - lowb;
+  const uint32_t A = vb & ((1u << ab) - 1u), B = vb >> ab;
+  const uint32_t hi = (jhi + 1u < 32u) ? (B << (jhi + 1u)) : 0u;
+  const uint32_t fixed = hi | (A << lowb);
+  const uint32_t lowmask = (1u << lowb) - 1u;
+  auto gidx = [&](uint32_t i) { return fixed | ((i >> lowb) << jlo) | (i & lowmask); };
+  const bool asc = ((fixed >> lv) & 1u) == 0u;
+  uint32_t v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = __ldcg(out + gidx(bt_elem<0>(threadIdx.x, r)));
+  const int b0 = (int)lowb - 8, b1 = (int)lowb - 4, b2 = (int)lowb;  // lowest register bit in use per pattern
+  if (asc) bt_levels_dir_from<true>(v, b0); else bt_levels_dir_from<false>(v, b0);
+  bt_store<0>(v, t);
+  __syncthreads();
+  bt_load<1>(v, t);
+  if (asc) bt_levels_dir_from<true>(v, b1); else bt_levels_dir_from<false>(v, b1);
+  bt_store<1>(v, t);
+  __syncthreads();
+  bt_load<2>(v, t);
+  if (asc) bt_levels_dir_from<true>(v, b2); else bt_levels_dir_from<false>(v, b2);
+  // positions 16t .. 16t + 15: groups of 4 are contiguous (runs of >= 4 keys)
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<uint4*>(out + gidx(16u * threadIdx.x + 4u * q)) =
+        make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
 // Full sort of a 4096-key tile (merge sizes 2 .. 4096), keys read from `in`.
 __device__ __forceinline__ void bitonic_tile_sort_regs(const uint32_t* in, uint32_t* out, uint32_t* t,
                                                        uint32_t gbase) {
@@ -899,16 +926,11 @@ __device__ __forceinline__ void bitonic_block(const kl_args_bitonic& a, uint32_t
   const uint32_t P = bitonic_tile_log2(L);
   const uint32_t tile_n = 1u << P;
   const BitonicStep st = bitonic_step(L, stage);
-  if (st.kind == 1) {
-    switch (st.jhi - st.jlo + 1) {
-      case 4: bitonic_fused<4>(a.out, vb, st.lv, st.jlo); break;
-      case 3: bitonic_fused<3>(a.out, vb, st.lv, st.jlo); break;
-      case 2: bitonic_fused<2>(a.out, vb, st.lv, st.jlo); break;
-      default: bitonic_fused<1>(a.out, vb, st.lv, st.jlo); break;
-    }
+  uint32_t* t = reinterpret_cast<uint32_t*>(smem);
+  if (st.kind == 1) {  // only when L > 12: the tile has 4096 keys
+    bitonic_high_pass(a.out, t, vb, st.lv, st.jhi, st.jlo);
     return;
   }
-  uint32_t* t = reinterpret_cast<uint32_t*>(smem);
   const uint32_t gbase = vb * tile_n;
   if (tile_n == 4096u) {
     if (st.kind == 0)
@@ -1175,6 +1197,32 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t 
           tmem_d),
       "l"(a), "l"(b), "r"(kBfIdesc), "r"(accum)
       : "memory");
+}
+// the same with the instruction descriptor given (other tile widths)
+__device__ __forceinline__ void umma_bf16_id(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t m, uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 lanes; one lane = one row
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");

@@ -152,14 +152,20 @@ def _oracle_profiles(K, rt):
     return gpu
 
 
-def test_mix_alone_equals_in_mix_and_decisions_match_oracle(K, T):
+@pytest.mark.parametrize("alpha", [None, (0.25, 0.12)])
+def test_mix_alone_equals_in_mix_and_decisions_match_oracle(K, T, alpha):
+    # alpha: pruning thresholds (alpha_p, alpha_m) of Section 4.3 on the device
+    # planner and the oracle alike; with (0.25, 0.12) every pair of types
+    # fewer than three apart below is pruned (their PUR and MUR gaps are both
+    # small), same-type pairs included
     from oracle import markov as mk
     from oracle import schedule as sc
     rng = np.random.default_rng(2)
     order = [t for t in MIX_SMALL for _ in range(2)]
     rng.shuffle(order)
     inps = [gen.gen_tenant(nm, 2, i, **MIX_SMALL[nm]) for i, nm in enumerate(order)]
-    rt = _runtime(K, slots_per_sm=4)
+    ap, am = alpha if alpha else (-1.0, -1.0)
+    rt = _runtime(K, slots_per_sm=4, alpha_p=ap, alpha_m=am)
     # known model inputs on both sides
     profs = []
     for t in range(K.KL_T_COUNT):
@@ -192,7 +198,11 @@ def test_mix_alone_equals_in_mix_and_decisions_match_oracle(K, T):
     for p in ph[1:-1]:
         R = [i for i in range(len(tens)) if (p.pending_mask >> i) & 1]
         assert len(R) == p.n_pending
-        cs = sc.find_coschedule(R, ot, model)
+        cs = sc.find_coschedule(R, ot, model, *(alpha or (None, None)))
+        if alpha and len(R) > 1:
+            # the device kept to the unpruned pairs whenever there was one
+            kept = sc.prune_pairs([(i, j) for i in R for j in R if i < j], ot, *alpha)
+            assert (p.A, p.B) in kept
         if (cs.A, cs.B) != (p.A, p.B if p.B >= 0 else None):
             # only a floating-point near-tie may differ
             assert abs(cs.cp - p.cp) < 1e-9, ((cs.A, cs.B, cs.cp), (p.A, p.B, p.cp))
