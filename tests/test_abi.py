@@ -61,7 +61,12 @@ def test_errors_without_gpu(K):
     assert L.kl_tenant_shape_of(K.KL_T_GEMM_F32, C.byref(g), C.sizeof(g), C.byref(sh)) == K.KL_EINVAL
     b = K.kl_args_bitonic(16, 32, 22, 0)
     sh = K.tenant_shape(K.KL_T_BITONIC, b)
-    assert sh.nstages == 29 and sh.grid[0] == 1024 and sh.total_blocks == 29 * 1024
+    # 2^22 keys in 4096-key tiles: the tile sort, then for each of the 10 merge
+    # sizes above the tile one pass over its distances above the tile (at most
+    # 10 of them) and one tile merge: 1 + 10 x 2 stages of 1024 blocks
+    assert sh.nstages == 21 and sh.grid[0] == 1024 and sh.total_blocks == 21 * 1024
+    b = K.kl_args_bitonic(16, 32, 30, 0)                    # merge sizes 2^23 .. 2^30 need two such passes
+    assert K.tenant_shape(K.KL_T_BITONIC, b).nstages == 1 + 10 * 2 + 8 * 3
     h = K.kl_args_hist256(16, 32, (1 << 26))
     sh = K.tenant_shape(K.KL_T_HIST256, h)
     assert sh.nstages == 2 and sh.grid[0] == 1 and sh.total_blocks == 1 + 2048
