@@ -47,8 +47,9 @@
 extern "C" {
 #endif
 
-#define KL_ABI_VERSION 1
-#define KL_BLOCK_THREADS 256     /* every tenant block has 256 threads          */
+#define KL_ABI_VERSION 2
+#define KL_BLOCK_THREADS 256     /* threads of a co-scheduler slot (and of every
+                                    tenant block but the resource-heavy variants) */
 #define KL_MAX_ARGS_BYTES 96     /* largest kl_args_* block                     */
 #define KL_MAX_SLOTS 8           /* per-SM block slots of the co-scheduler      */
 
@@ -87,8 +88,20 @@ typedef enum {
     KL_T_SAD = 12,          /* sums of absolute differences, 4x4 blocks, motion search */
     KL_T_STENCIL = 13,      /* 7-point stencil on a 3-D grid */
     KL_T_MRIQ = 14,         /* MRI Q matrix: phiMag, then Q over the k-space samples */
-    KL_T_COUNT = 15
+    KL_T_TESTMIX = 15,      /* Section 4.3 testing kernel: a tunable mix of streaming loads
+                               and dependent fused multiply-adds (PUR / MUR sweep)        */
+    /* Resource-heavy variants (their blocks do not fit a co-scheduler slot of
+     * 256 threads at 64 registers; each runs in a resource-class kernel of its
+     * own, one CTA per SM beside two co-scheduler slots, Section 6's merged-
+     * kernel register cost): */
+    KL_T_BS255 = 16,        /* Black-Scholes, 128-thread blocks of 16 options a thread
+                               held in registers (up to 255 per thread)                 */
+    KL_T_HIST1024 = 17,     /* 256-bin histogram with 1024-thread blocks                 */
+    KL_T_GEMM_F32_BIG = 18, /* FP32 GEMM, 128x128 tiles staged in 96 KB of shared memory */
+    KL_T_COUNT = 19
 } kl_tenant_type;
+#define KL_T_MAIN_COUNT 16  /* types 0 .. 15 run in the co-scheduler's slots; the
+                               planner of Algorithm 1 pairs these                         */
 
 /* ----------------------------------------------------------- tenant arguments
  * Layouts: row-major, densely packed, element types as named. Pointers to
@@ -215,12 +228,30 @@ typedef struct {            /* KL_T_MRIQ: stage 0 = phiMag (256 samples per bloc
     uint32_t numK, numX;
 } kl_args_mriq;
 
+typedef struct {            /* KL_T_TESTMIX: thread g of the grid (256 a block) runs
+                               `iters` rounds of `mem` streaming loads
+                               acc += in[(g + (i mem + m) nthreads) mod n_in] then
+                               `alu` dependent steps acc = fma(acc, c1, c2), and
+                               stores out[g] = acc                                     */
+    const float* in;        /* [n_in], n_in a power of two                              */
+    float* out;             /* [nthreads]                                               */
+    uint32_t n_in, nthreads;
+    uint32_t iters, mem, alu, pad;
+    float c1, c2;
+} kl_args_testmix;
+
+/* KL_T_BS255 takes kl_args_blackscholes (128 threads x 16 options = 2048
+ * options per block); KL_T_HIST1024 takes kl_args_hist256 (stage 0 clears,
+ * stage 1 counts 131072 bytes per 1024-thread block); KL_T_GEMM_F32_BIG takes
+ * kl_args_gemm_f32 (one 128 x 128 tile of C per block; N, K multiples of 4). */
+
 /* Launch shape of a tenant as a plain kernel would use it (Section 2.2: a
  * kernel is k thread blocks). Multi-stage tenants (histogram, bitonic sort)
  * are a chain of grids; stage s may start only when stage s-1 has finished. */
 typedef struct {
     uint32_t grid[3];       /* blocks of stage 0 (x, y, z)                      */
-    uint32_t block[3];      /* {256, 1, 1}                                      */
+    uint32_t block[3];      /* {256, 1, 1}; {128, 1, 1} for KL_T_BS255, {1024, 1, 1}
+                               for KL_T_HIST1024                                 */
     uint32_t nstages;
     uint32_t smem_bytes;    /* dynamic shared memory per block                  */
     uint64_t total_blocks;  /* summed over stages                               */
@@ -230,7 +261,7 @@ typedef struct {
 typedef struct {
     uint32_t type;              /* kl_tenant_type                                */
     uint32_t grid[3];           /* must equal kl_tenant_shape().grid             */
-    uint32_t block[3];          /* must be {256, 1, 1}                           */
+    uint32_t block[3];          /* must equal kl_tenant_shape().block            */
     uint32_t smem_bytes;        /* resource profile: declared dynamic smem       */
     uint32_t regs_per_thread;   /* resource profile: declared registers (0 = n/a) */
     uint32_t slice_blocks;      /* blocks per slice; 0 = runtime's per-type size */
@@ -276,8 +307,9 @@ typedef enum {
                                instead of the largest-CP pair */
 #define KL_CFG_LIGHT_BUILD 128u /* a batch run whose kernels are all of the light
                                types (gather, Black-Scholes, SpMV, triad,
-                               escape-time, MatrixAdd, TEA, stencil: short
-                               bodies within 32 registers) uses the co-scheduler
+                               escape-time, MatrixAdd, TEA, stencil, the testing
+                               kernel: short bodies within 32 registers), with no
+                               resource-heavy variant, uses the co-scheduler
                                build with 8 CTAs per SM instead of 4, and the CP
                                table for 8 slots; needs slots_per_sm = 0 and no
                                kl_set_cp_table override; default on */
@@ -387,6 +419,9 @@ typedef struct {
                                    slice to pull (idle slots)                    */
     uint64_t stage_wait_ns;     /* ... time at a stage barrier inside a slice     */
     uint64_t plan_ns;           /* ... time re-planning (FindCoSchedule)          */
+    uint32_t class_ctas[4];     /* per resource class (index 1..3: KL_T_BS255,
+                                   KL_T_HIST1024, KL_T_GEMM_F32_BIG): CTAs of its
+                                   class kernel that found work; [0] unused      */
 } kl_run_stats;
 
 typedef enum {
@@ -619,10 +654,11 @@ int kl_count_pruned(const double* pur, const double* mur, uint32_t n, double alp
  * NULL) and returns after the run has completed: it synchronizes that stream.
  * It calls no cudaMalloc, cudaFree or other allocating routine: the device
  * queue, run state and phase log live in a fixed file-scope device array of
- * the library (KL_NOALLOC_SCRATCH_BYTES = 95,232 bytes, held by every GPU that
+ * the library (KL_NOALLOC_SCRATCH_BYTES = 97,536 bytes, held by every GPU that
  * loads the library until the process exits), and the host-side descriptor
- * image lives on the caller's stack (about 21.5 KB).
- *   descs, n        kernel descriptors as for kl_submit; 1 <= n <=
+ * image lives on the caller's stack (about 23.5 KB).
+ *   descs, n        kernel descriptors as for kl_submit, of the co-scheduler's
+ *                   types (type < KL_T_MAIN_COUNT, else KL_EINVAL); 1 <= n <=
  *                   KL_NOALLOC_MAX_TENANTS, else KL_EOVERFLOW (n = 0: KL_EINVAL);
  *                   slice_blocks = 0 takes the runtime's built-in slice of the
  *                   type (no profiles are loaded here)
@@ -643,7 +679,7 @@ int kl_count_pruned(const double* pur, const double* mur, uint32_t n, double alp
  * call's contents (each call rewrites what must start at zero); calls whose
  * GPU work overlaps race on it and must not be issued concurrently. */
 #define KL_NOALLOC_MAX_TENANTS 64
-#define KL_NOALLOC_SCRATCH_BYTES 95232
+#define KL_NOALLOC_SCRATCH_BYTES 97536
 int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const double* cp_table,
                    const uint32_t* slots_a_table, void* cuda_stream, uint64_t wait_limit_ns,
                    int32_t* states);

@@ -159,6 +159,23 @@ void or_blackscholes(const float* S, const float* K, const float* r, const float
     }
 }
 
+/* ------------------------------------------------------------ testing kernel (Section 4.3)
+ * Thread g of nthreads: acc = 0; for round i < iters: for m < mem:
+ * acc = acc + in[(g + (i mem + m) nthreads) mod n_in]; then alu times
+ * acc = fmaf(acc, c1, c2); out[g] = acc. */
+
+void or_testmix(const float* in, float* out, int64_t n_in, int64_t nthreads, int64_t iters, int64_t mem,
+                int64_t alu, float c1, float c2) {
+    for (int64_t g = 0; g < nthreads; ++g) {
+        float acc = 0.0f;
+        for (int64_t i = 0; i < iters; ++i) {
+            for (int64_t m = 0; m < mem; ++m) acc = acc + in[(g + (i * mem + m) * nthreads) % n_in];
+            for (int64_t q = 0; q < alu; ++q) acc = fmaf(acc, c1, c2);
+        }
+        out[g] = acc;
+    }
+}
+
 /* ------------------------------------------------------------ gather */
 
 void or_gather(const int32_t* a, const int32_t* idx, int32_t* out, int64_t lo, int64_t hi) {

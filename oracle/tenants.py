@@ -42,6 +42,7 @@ def lib():
         _lib.or_logf.argtypes = [C.c_float]; _lib.or_logf.restype = C.c_float
         _lib.or_blackscholes.argtypes = [f32p] * 7 + [L]
         _lib.or_gather.argtypes = [i32p, i32p, i32p, L, L]
+        _lib.or_testmix.argtypes = [f32p, f32p, L, L, L, L, L, C.c_float, C.c_float]
         _lib.or_gemm_f32.argtypes = [f32p, f32p, f32p, L, L, L]
         _lib.or_gemm_f32_sample.argtypes = [f32p, f32p, i64p, i64p, f32p, L, L, L]
         _lib.or_spmv_csr.argtypes = [i32p, i32p, f32p, f32p, f32p, f64p, f64p, L]
@@ -79,6 +80,14 @@ def blackscholes(S, K, r, v, T):
     lib().or_blackscholes(_c(S, np.float32), _c(K, np.float32), _c(r, np.float32),
                           _c(v, np.float32), _c(T, np.float32), call, put, n)
     return call, put
+
+
+def testmix(inp):
+    """The Section 4.3 testing kernel's definition (oracle/tenants.c or_testmix)."""
+    out = np.empty(inp["nthreads"], np.float32)
+    lib().or_testmix(_c(inp["data"], np.float32), out, inp["n_in"], inp["nthreads"], inp["iters"], inp["mem"],
+                     inp["alu"], float(inp["c1"]), float(inp["c2"]))
+    return out
 
 
 def gather(a, idx, lo=0, hi=None, out=None):

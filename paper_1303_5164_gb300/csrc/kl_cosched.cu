@@ -173,7 +173,7 @@ struct ScanPart {
   uint32_t nlow, nms;
   int32_t lowp[kFill + 2];
   int32_t lowms[4];
-  int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
+  int32_t low1[KL_T_MAIN_COUNT], low2[KL_T_MAIN_COUNT];
 };
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kPlanScratch = sizeof(ScanPart) * kWarps + 16;
@@ -200,9 +200,9 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
   __syncthreads();
   const uint32_t lo = bounds[0], hi = bounds[1];
   {
-    int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
+    int32_t low1[KL_T_MAIN_COUNT], low2[KL_T_MAIN_COUNT];
 #pragma unroll
-    for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
+    for (int t = 0; t < KL_T_MAIN_COUNT; ++t) low1[t] = low2[t] = -1;
     uint32_t npend = 0, nlow = 0, nms = 0;
     unsigned long long pmask = 0ull;
     int32_t lowp[kFill + 2], lowms[4];
@@ -219,7 +219,8 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
         const TenantDev& d = tenant(T, R, i);
         // static fields through L2: in serving mode the slot may have been refilled
         ty = __ldcg(&d.type);
-        pend = ld_relaxed(&d.next) < __ldcg(&d.total);
+        // kernels of the resource-heavy classes are their class kernels' business
+        pend = ld_relaxed(&d.next) < __ldcg(&d.total) && tn::resource_class(ty) == tn::kClassMain;
         multi = __ldcg(&d.nstages) > 1u;
       }
       const uint32_t pb = __ballot_sync(0xffffffffu, pend);
@@ -230,7 +231,7 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
       const uint32_t msb = __ballot_sync(0xffffffffu, pend && multi);
       for (uint32_t m = msb; m && nms < 4; m &= m - 1) lowms[nms++] = (int32_t)(base + __ffs(m) - 1);
 #pragma unroll
-      for (int t = 0; t < KL_T_COUNT; ++t) {
+      for (int t = 0; t < KL_T_MAIN_COUNT; ++t) {
         uint32_t m = __ballot_sync(0xffffffffu, pend && ty == (uint32_t)t);
         if (m && low1[t] < 0) {
           low1[t] = (int32_t)(base + __ffs(m) - 1);
@@ -249,7 +250,7 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
       for (uint32_t f = 0; f < nlow; ++f) q.lowp[f] = lowp[f];
       for (uint32_t f = 0; f < nms; ++f) q.lowms[f] = lowms[f];
 #pragma unroll
-      for (int t = 0; t < KL_T_COUNT; ++t) {
+      for (int t = 0; t < KL_T_MAIN_COUNT; ++t) {
         q.low1[t] = low1[t];
         q.low2[t] = low2[t];
       }
@@ -258,8 +259,8 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
   __syncthreads();
   if (threadIdx.x != 0) return;
   // merge in warp order (warp w scanned lower sequence numbers than warp w+1)
-  int32_t low1[KL_T_COUNT], low2[KL_T_COUNT];
-  for (int t = 0; t < KL_T_COUNT; ++t) low1[t] = low2[t] = -1;
+  int32_t low1[KL_T_MAIN_COUNT], low2[KL_T_MAIN_COUNT];
+  for (int t = 0; t < KL_T_MAIN_COUNT; ++t) low1[t] = low2[t] = -1;
   uint32_t npend = 0, nlow = 0, nms = 0;
   unsigned long long pmask = 0ull;
   int32_t lowp[kFill + 2], lowms[4];
@@ -271,7 +272,7 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
     if (first_pending < 0) first_pending = q.first;
     for (uint32_t f = 0; f < q.nlow && nlow < (uint32_t)kFill + 2u; ++f) lowp[nlow++] = q.lowp[f];
     for (uint32_t f = 0; f < q.nms && nms < 4; ++f) lowms[nms++] = q.lowms[f];
-    for (int t = 0; t < KL_T_COUNT; ++t) {
+    for (int t = 0; t < KL_T_MAIN_COUNT; ++t) {
       const int32_t c[2] = {q.low1[t], q.low2[t]};
       for (int k = 0; k < 2; ++k) {
         if (c[k] < 0) break;
@@ -296,7 +297,7 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
   ph.intake_seen = hi;
   ph.pad2 = 0;
   if (npend == 1) {
-    for (int t = 0; t < KL_T_COUNT; ++t)
+    for (int t = 0; t < KL_T_MAIN_COUNT; ++t)
       if (low1[t] >= 0) ph.A = low1[t];
   } else if (npend >= 2) {
     int32_t aged = -1;
@@ -305,12 +306,12 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
     if ((R->flags & KL_CFG_RANDOM_PLAN) && R->slots >= 2) {
       const unsigned long long r = splitmix64(R->plan_seed ^ (0xD1B54A32D192ED03ull * (seq_old + 1ull)));
       uint32_t nc = 0;
-      for (int ta = 0; ta < KL_T_COUNT; ++ta)
-        for (int tb = ta; tb < KL_T_COUNT; ++tb)
+      for (int ta = 0; ta < KL_T_MAIN_COUNT; ++ta)
+        for (int tb = ta; tb < KL_T_MAIN_COUNT; ++tb)
           nc += low1[ta] >= 0 && (ta == tb ? low2[ta] >= 0 : low1[tb] >= 0);
       uint32_t pick = (uint32_t)((r & 0xFFFFFFFFull) % nc);
-      for (int ta = 0; ta < KL_T_COUNT && aged < 0; ++ta)
-        for (int tb = ta; tb < KL_T_COUNT && aged < 0; ++tb) {
+      for (int ta = 0; ta < KL_T_MAIN_COUNT && aged < 0; ++ta)
+        for (int tb = ta; tb < KL_T_MAIN_COUNT && aged < 0; ++tb) {
           if (!(low1[ta] >= 0 && (ta == tb ? low2[ta] >= 0 : low1[tb] >= 0))) continue;
           if (pick-- != 0u) continue;
           ph.A = min(low1[ta], ta == tb ? low2[ta] : low1[tb]);
@@ -332,7 +333,7 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
       double best = 0.0;
       int32_t bj = -1;
       for (int pass = 0; pass < 2 && bj < 0; ++pass)
-        for (int tb = 0; tb < KL_T_COUNT; ++tb) {
+        for (int tb = 0; tb < KL_T_MAIN_COUNT; ++tb) {
           const int32_t j = low1[tb] != aged ? low1[tb] : low2[tb];
           if (j < 0) continue;
           const uint32_t tyj = tenant(T, R, (uint32_t)j).type;
@@ -354,9 +355,9 @@ __device__ __noinline__ void replan(TenantDev* T, RunDev* R, PhaseDev* P, uint32
     for (int pass = 0; pass < 2 && aged < 0; ++pass) {
       double best = 0.0;
       int32_t bi = -1, bj = -1;
-      for (int ta = 0; ta < KL_T_COUNT; ++ta) {
+      for (int ta = 0; ta < KL_T_MAIN_COUNT; ++ta) {
         if (low1[ta] < 0) continue;
-        for (int tb = ta; tb < KL_T_COUNT; ++tb) {
+        for (int tb = ta; tb < KL_T_MAIN_COUNT; ++tb) {
           int32_t i, j;
           if (ta == tb) {
             if (low2[ta] < 0) continue;
@@ -568,10 +569,13 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
   if (tid == 0) {
     const uint32_t sm = smid() & (kMaxSM - 1);
     const uint32_t ticket = atomicAdd(&R->sm_ticket[sm], 1u);
-    s_slot = ticket % R->slots;
+    // with resource classes beside it the grid carries extra CTAs and each
+    // SM keeps `slots` of them; the others leave at once, freeing the room
+    s_slot = (R->quota_exit && ticket >= R->slots) ? 0xffffffffu : ticket % R->slots;
     atomicCAS(&R->t_launch, 0ull, gtimer());
   }
   __syncthreads();
+  if (s_slot == 0xffffffffu) return;
   const tn::BlockCtx tcx{&s_tmem, &R->error, R->wait_limit_ns};
   if constexpr (BUILD == tn::kBuildFull) tn::acquire_tmem(tcx);
   if (R->serve && blockIdx.x == 0) {
@@ -596,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
     if (tid == 0) {
       const uint32_t slot = s_slot;
       const uint32_t S = R->slots;
-      const uint32_t n_sm = gridDim.x / S;
+      const uint32_t n_sm = R->n_sm;
       const unsigned long long limit = R->wait_limit_ns;
       ctl.action = kActWait;
       ctl.tenant = -1;
@@ -724,7 +728,9 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
             bool prefix = true;
             for (uint32_t j = c0; j < R->n_tenants && j < c0 + 8u; ++j) {
               uint32_t g0 = 0, g1 = 0;
-              const int r = try_pull(T, R, (int32_t)j, 0u, n_sm, g0, g1);
+              const int r = tn::resource_class(__ldcg(&tenant(T, R, j).type)) != tn::kClassMain
+                                ? kExhausted  // a class kernel's kernel: not for this slot
+                                : try_pull(T, R, (int32_t)j, 0u, n_sm, g0, g1);
               if (r == kPulled) {
                 ctl.action = kActRun;
                 ctl.tenant = (int32_t)j;
@@ -788,7 +794,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
       // slice instead: that is where arrivals are noticed.
       uint32_t pf_a = 0xffffffffu, pf_seq = 0;  // the only values held across the blocks
       if (tid == 0 && ctl.own && !R->serve && d.nstages == 1u) {
-        const uint32_t S = R->slots, n_sm = gridDim.x / S;
+        const uint32_t S = R->slots, n_sm = R->n_sm;
         const uint32_t sl = d.slice;
         if ((uint64_t)g1 + 2ull * S * n_sm * sl < (uint64_t)d.total) {
           pf_a = atomicAdd(&d.next, sl);
@@ -848,6 +854,149 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BUILD)) cosched_kernel(T
     atomicAdd(&R->plan_ns, ctl.acc_plan);
     atomicAdd(&R->ctas_done, 1u);
   }
+}
+
+// ------------------------------------------------------------------ resource classes
+// A resource-heavy tenant type (tn::resource_class != 0) cannot run in a
+// co-scheduler slot: its blocks need more threads, registers or shared memory
+// than a slot holds, and compiling it into the co-scheduler would raise every
+// slot's resources to its size (the merged-kernel cost of Section 6). It runs
+// in a persistent kernel of its own, launched after the co-scheduler for the
+// run with two CTAs per SM. The co-scheduler keeps two slots per SM (its
+// further CTAs leave at once), which leaves room for one class CTA beside them
+// on every SM; the other class CTAs wait for room and take over as the
+// co-scheduler's kernels, or another class's, run out. A class CTA pulls
+// slices of its class's kernels in submission order from the same device
+// queues and leaves when none has blocks left; it never waits on the
+// co-scheduler or another class, nor they on it.
+template <int TYPE>
+__device__ __forceinline__ void class_block(const void* args, const tn::Stage& st, uint32_t vb, char* smem) {
+  if constexpr (TYPE == KL_T_BS255)
+    tn::bs255_block(*reinterpret_cast<const kl_args_blackscholes*>(args), vb);
+  else if constexpr (TYPE == KL_T_HIST1024)
+    tn::hist1024_block(*reinterpret_cast<const kl_args_hist256*>(args), st.s, vb, smem);
+  else if constexpr (TYPE == KL_T_GEMM_F32_BIG)
+    tn::gemm_big_block(*reinterpret_cast<const kl_args_gemm_f32*>(args), vb, smem);
+}
+
+template <int TYPE>
+__global__ void __launch_bounds__(tn::block_threads(TYPE), 2) class_kernel(TenantDev* __restrict__ T,
+                                                                          RunDev* __restrict__ R) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int s_go;
+  __shared__ int32_t s_t;
+  __shared__ uint32_t s_g0, s_g1, s_fail;
+  __shared__ __align__(16) unsigned char s_args[KL_MAX_ARGS_BYTES];
+  constexpr int C = tn::resource_class(TYPE);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_go = 0;
+    s_t = -1;
+    atomicCAS(&R->t_launch, 0ull, gtimer());
+  }
+  __syncthreads();
+  uint32_t cursor = 0;  // kernels below it have handed out every block (thread 0)
+  for (;;) {
+    if (tid == 0) {
+      s_t = -2;  // -2: nothing left for the class; >= 0: a slice was pulled
+      const unsigned long long t0 = gtimer();
+      for (;;) {
+        if (ld_relaxed(reinterpret_cast<uint32_t*>(&R->error)) != 0) break;
+        bool blocked = false;
+        for (uint32_t j = cursor; j < R->n_tenants; ++j) {
+          if (__ldcg(&tenant(T, R, j).type) != (uint32_t)TYPE) {
+            if (j == cursor) ++cursor;
+            continue;
+          }
+          uint32_t g0 = 0, g1 = 0;
+          const int r = try_pull(T, R, (int32_t)j, 0u, R->n_sm, g0, g1);
+          if (r == kPulled) {
+            s_t = (int32_t)j;
+            s_g0 = g0;
+            s_g1 = g1;
+            break;
+          }
+          if (r == kExhausted && j == cursor)
+            ++cursor;
+          else if (r == kBlocked)
+            blocked = true;
+        }
+        if (s_t >= 0 || !blocked) break;
+        if (gtimer() - t0 > R->wait_limit_ns) {  // a stage barrier that never opens
+          set_error(R, KL_EDEVICE_TIMEOUT, 5u);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __syncthreads();
+    const int32_t t = s_t;
+    if (t < 0) break;
+    if (tid == 0 && !s_go) {
+      s_go = 1;
+      atomicAdd(&R->cls_ctas[C], 1u);  // a CTA of the class that found work
+    }
+    TenantDev& d = tenant(T, R, (uint32_t)t);
+    if (tid < (int)(KL_MAX_ARGS_BYTES / 16))
+      reinterpret_cast<uint4*>(s_args)[tid] = __ldcg(reinterpret_cast<const uint4*>(d.args) + tid);
+    __syncthreads();
+    for (uint32_t g = s_g0; g < s_g1;) {
+      const tn::Stage st = stage_at(d, (uint32_t)TYPE, g);
+      if (st.begin > 0) {
+        if (tid == 0) {
+          s_fail = 0;
+          const unsigned long long since = gtimer();
+          while (ld_acquire(&d.done) < st.begin) {
+            if (gtimer() - since > R->wait_limit_ns) {
+              set_error(R, KL_EDEVICE_TIMEOUT, 6u);
+              s_fail = 1;
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+        __syncthreads();
+        if (s_fail) break;
+      }
+      const uint32_t ge = min(s_g1, st.end);
+      for (uint32_t b = g; b < ge; ++b) {
+        class_block<TYPE>(s_args, st, b - st.begin, smem);
+        __syncthreads();
+      }
+      if (tid == 0) {
+        if (d.nstages > 1) __threadfence();
+        const uint32_t cnt = ge - g;
+        const uint32_t old = atomicAdd(&d.done, cnt);
+        if (old + cnt == d.total) complete_tenant(d, R);
+      }
+      g = ge;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) atomicAdd(&R->ctas_done, 1u);
+}
+
+int class_launch(int type, TenantDev* T, RunDev* R, uint32_t grid, cudaStream_t stream) {
+  const uint32_t smem = tn::smem_bytes((uint32_t)type);
+  switch (type) {
+    case KL_T_BS255: class_kernel<KL_T_BS255><<<grid, tn::block_threads(KL_T_BS255), smem, stream>>>(T, R); break;
+    case KL_T_HIST1024:
+      class_kernel<KL_T_HIST1024><<<grid, tn::block_threads(KL_T_HIST1024), smem, stream>>>(T, R);
+      break;
+    case KL_T_GEMM_F32_BIG: {
+      static bool attr = false;
+      if (!attr) {
+        if (cudaFuncSetAttribute(class_kernel<KL_T_GEMM_F32_BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+          return -1;
+        attr = true;
+      }
+      class_kernel<KL_T_GEMM_F32_BIG><<<grid, tn::block_threads(KL_T_GEMM_F32_BIG), smem, stream>>>(T, R);
+      break;
+    }
+    default: return -1;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Run staging through the SMs: copies between the runtime's pinned host image
@@ -912,8 +1061,8 @@ int cosched_occupancy(int* ctas_per_sm, int build) {
 }
 
 int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
-                   int build, cudaStream_t stream) {
-  dim3 grid(n_sm * slots), block(kThreads);
+                   int build, cudaStream_t stream, uint32_t extra_ctas) {
+  dim3 grid(n_sm * slots + extra_ctas), block(kThreads);
   switch (build) {
     case tn::kBuildPlain: cosched_kernel<tn::kBuildPlain><<<grid, block, smem_bytes, stream>>>(T, R, P); break;
     case tn::kBuildFull: cosched_kernel<tn::kBuildFull><<<grid, block, smem_bytes, stream>>>(T, R, P); break;

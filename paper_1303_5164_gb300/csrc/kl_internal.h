@@ -136,6 +136,11 @@ struct alignas(128) RunDev {
   unsigned long long plan_ns;        // summed over CTAs: time re-planning
   alignas(128) uint32_t fill_cursor; // deep fill: kernels below this one are all drained
   alignas(128) uint32_t sm_ticket[kMaxSM];
+  // ---- resource classes (static, host-written)
+  uint32_t n_sm;                      // SMs of the device (the grid may carry extra CTAs)
+  uint32_t quota_exit;                // 1: main CTAs past `slots` on their SM exit at once
+  // ---- resource classes (dynamic, zero at launch)
+  uint32_t cls_ctas[4];               // CTAs of class c that found work (index 0 unused)
 };
 
 // One device-side copy (kl_cosched.cu, stage_copy): dst and src are

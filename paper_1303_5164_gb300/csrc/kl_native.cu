@@ -30,6 +30,32 @@ __global__ void __launch_bounds__(kThreads) native_kernel(ArgsBlob args, uint32_
   if constexpr (TYPE == KL_T_GEMM_BF16) tn::release_tmem(cx);
 }
 
+// Plain launches of the resource-heavy variants, at their own block sizes.
+template <int TYPE>
+__global__ void __launch_bounds__(tn::block_threads(TYPE), 1) native_heavy_kernel(ArgsBlob args, uint32_t stage) {
+  extern __shared__ __align__(16) char smem[];
+  const tn::Stage st{stage, 0u, 0u};
+  if constexpr (TYPE == KL_T_BS255)
+    tn::bs255_block(*reinterpret_cast<const kl_args_blackscholes*>(args.b), blockIdx.x);
+  else if constexpr (TYPE == KL_T_HIST1024)
+    tn::hist1024_block(*reinterpret_cast<const kl_args_hist256*>(args.b), st.s, blockIdx.x, smem);
+  else if constexpr (TYPE == KL_T_GEMM_F32_BIG)
+    tn::gemm_big_block(*reinterpret_cast<const kl_args_gemm_f32*>(args.b), blockIdx.x, smem);
+}
+
+template <int TYPE>
+static cudaError_t launch_heavy(const void* args, uint32_t stage, uint32_t blocks, cudaStream_t s) {
+  ArgsBlob blob;
+  memcpy(blob.b, args, KL_MAX_ARGS_BYTES);
+  const uint32_t sm = tn::smem_bytes(TYPE);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(native_heavy_kernel<TYPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  native_heavy_kernel<TYPE><<<blocks, tn::block_threads(TYPE), sm, s>>>(blob, stage);
+  return cudaGetLastError();
+}
+
 template <int TYPE>
 static cudaError_t launch_one(const void* args, uint32_t stage, uint32_t blocks, cudaStream_t s) {
   ArgsBlob blob;
@@ -287,6 +313,10 @@ int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s) {
       case KL_T_SAD: e = launch_one<KL_T_SAD>(args, st, nb, s); break;
       case KL_T_STENCIL: e = launch_one<KL_T_STENCIL>(args, st, nb, s); break;
       case KL_T_MRIQ: e = launch_one<KL_T_MRIQ>(args, st, nb, s); break;
+      case KL_T_TESTMIX: e = launch_one<KL_T_TESTMIX>(args, st, nb, s); break;
+      case KL_T_BS255: e = launch_heavy<KL_T_BS255>(args, st, nb, s); break;
+      case KL_T_HIST1024: e = launch_heavy<KL_T_HIST1024>(args, st, nb, s); break;
+      case KL_T_GEMM_F32_BIG: e = launch_heavy<KL_T_GEMM_F32_BIG>(args, st, nb, s); break;
       default: return -1;
     }
     if (e != cudaSuccess) return -1;

@@ -26,7 +26,7 @@
 namespace kl {
 int cosched_occupancy(int* ctas_per_sm, int build);
 int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
-                   int build, cudaStream_t stream);
+                   int build, cudaStream_t stream, uint32_t extra_ctas = 0);
 
 namespace {
 
@@ -39,8 +39,8 @@ constexpr size_t kRunOff = sizeof(TenantDev) * kMaxT;
 constexpr size_t kPhaseOff = (kRunOff + sizeof(RunDev) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kPhaseOff + sizeof(PhaseDev) * kPhaseSlots;
 constexpr int kMaxDevices = 64;
-// the sizes the header documents: 64 x 256 B tenants + the 4,992 B run state
-// (rounded to 5,120 B) + 512 x 144 B phases; the phase ring is a power of two,
+// the sizes the header documents: 64 x 256 B tenants + the 7,296 B run state
+// (rounded to 7,424 B) + 512 x 144 B phases; the phase ring is a power of two,
 // so 512 slots for the at most 4 x 64 + 16 = 272 phases of a run
 static_assert(kScratchBytes == KL_NOALLOC_SCRATCH_BYTES, "documented size of the device array");
 
@@ -58,7 +58,7 @@ struct HostImage {
   RunDev run;
   PhaseDev ph0;
 };
-static_assert(sizeof(HostImage) <= 21760, "documented size of the stack image");
+static_assert(sizeof(HostImage) <= 23936, "documented size of the stack image");
 
 }  // namespace
 }  // namespace kl
@@ -100,7 +100,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
   for (uint32_t i = 0; i < n; ++i) {
     const kl_kernel_desc& d = descs[i];
     kl_tenant_shape sh;
-    if (d.type >= KL_T_COUNT || !d.args) return KL_EINVAL;
+    if (d.type >= KL_T_MAIN_COUNT || !d.args) return KL_EINVAL;  // the co-scheduler's types only
     int rc = kl_tenant_shape_of(d.type, d.args, d.args_size, &sh);
     if (rc) return rc;
     if (d.block[0] != KL_BLOCK_THREADS || d.block[1] != 1 || d.block[2] != 1) return KL_EINVAL;
@@ -124,6 +124,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
   RunDev& R = img.run;
   R.n_tenants = n;
   R.slots = S;
+  R.n_sm = n_sm;
   R.max_phases = 4 * n + 16;
   R.n_types = KL_T_COUNT;
   R.flags = KL_CFG_BACKFILL;
@@ -150,7 +151,7 @@ extern "C" int kl_run_noalloc(const kl_kernel_desc* descs, uint32_t n, const dou
       cudaMemcpyAsync(dP, &img.ph0, sizeof(PhaseDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return KL_ECUDA;
   bool tc = false;
-  for (uint32_t i = 0; i < n; ++i) tc |= !tn::in_plain_build(descs[i].type);
+  for (uint32_t i = 0; i < n; ++i) tc |= !tn::in_plain_build(descs[i].type);  // a full-build type
   if (cosched_launch(dT, dR, dP, n_sm, S, tn::kMaxTenantSmem, tc ? tn::kBuildFull : tn::kBuildPlain, s) != 0)
     return KL_ECUDA;
   if (cudaMemcpyAsync(img.t, dT, sizeof(TenantDev) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

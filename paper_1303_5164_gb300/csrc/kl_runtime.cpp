@@ -30,9 +30,10 @@
 namespace kl {
 int cosched_occupancy(int* ctas_per_sm, int build);
 int cosched_launch(TenantDev* T, RunDev* R, PhaseDev* P, uint32_t n_sm, uint32_t slots, uint32_t smem_bytes,
-                   int build, cudaStream_t stream);
+                   int build, cudaStream_t stream, uint32_t extra_ctas = 0);
 int native_launch_tenant(uint32_t type, const void* args, cudaStream_t s);
 int stage_copy(const CopySeg* segs, uint32_t n, cudaStream_t s);
+int class_launch(int type, TenantDev* T, RunDev* R, uint32_t grid, cudaStream_t stream);
 namespace model {
 int pair(const kl_model_params& g, const kl_profile& pa, const kl_profile& pb, uint32_t slots, int states,
          uint32_t policy, uint32_t fixed_a, double* cA, double* cB, double* cpv, double* dT, double* solo,
@@ -68,6 +69,10 @@ size_t args_size_of(uint32_t type) {
     case KL_T_SAD: return sizeof(kl_args_sad);
     case KL_T_STENCIL: return sizeof(kl_args_stencil);
     case KL_T_MRIQ: return sizeof(kl_args_mriq);
+    case KL_T_TESTMIX: return sizeof(kl_args_testmix);
+    case KL_T_BS255: return sizeof(kl_args_blackscholes);
+    case KL_T_HIST1024: return sizeof(kl_args_hist256);
+    case KL_T_GEMM_F32_BIG: return sizeof(kl_args_gemm_f32);
     default: return 0;
   }
 }
@@ -77,6 +82,15 @@ bool a16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // Argument checks a plain launch of the tenant would need to be safe.
 int validate_args(uint32_t type, const void* a) {
   switch (type) {
+    // the resource-heavy variants take their base type's arguments
+    case KL_T_BS255: return validate_args(KL_T_BLACKSCHOLES, a);
+    case KL_T_HIST1024: return validate_args(KL_T_HIST256, a);
+    case KL_T_GEMM_F32_BIG: return validate_args(KL_T_GEMM_F32, a);
+    case KL_T_TESTMIX: {
+      const kl_args_testmix* t = (const kl_args_testmix*)a;
+      if (!t->in || !t->out || t->n_in == 0 || (t->n_in & (t->n_in - 1)) || t->nthreads == 0) return KL_EINVAL;
+      return KL_OK;
+    }
     case KL_T_GATHER: {
       const kl_args_gather* g = (const kl_args_gather*)a;
       if (!g->a || !g->idx || !g->out || g->n == 0 || !a16(g->idx) || !a16(g->out)) return KL_EINVAL;
@@ -189,6 +203,10 @@ kl_profile builtin_profile(uint32_t type) {
     case KL_T_SAD: p.R_m = 0.25; p.f_u = 0.3; p.L0 = 500; p.I_block = 8 * 150; p.PUR = 0.40; p.MUR = 0.10; break;
     case KL_T_STENCIL: p.R_m = 0.2; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 60; p.PUR = 0.20; p.MUR = 0.60; break;
     case KL_T_MRIQ: p.R_m = 0.001; p.f_u = 0.0; p.L0 = 500; p.I_block = 8 * 20000; p.PUR = 0.85; p.MUR = 0.01; break;
+    case KL_T_TESTMIX: p.R_m = 0.10; p.f_u = 0.0; p.L0 = 900; p.I_block = 8 * 400; p.PUR = 0.40; p.MUR = 0.40; break;
+    case KL_T_BS255: p = builtin_profile(KL_T_BLACKSCHOLES); p.warps_per_block = 4; p.I_block *= 8; break;
+    case KL_T_HIST1024: p = builtin_profile(KL_T_HIST256); p.warps_per_block = 32; p.I_block *= 16; break;
+    case KL_T_GEMM_F32_BIG: p = builtin_profile(KL_T_GEMM_F32); p.I_block *= 16; break;
     default: p.valid = 0; break;
   }
   return p;
@@ -314,6 +332,7 @@ void split_handle(kl_handle h, uint64_t* run, uint32_t* idx) {
 // pruning). Cached until profiles, parameters or the type set change.
 int ensure_table(kl_runtime* rt, uint32_t mask, uint32_t S) {
   if (rt->table_override) return KL_OK;
+  mask &= (1u << KL_T_MAIN_COUNT) - 1u;  // the planner pairs the co-scheduler's types only
   const bool same = rt->table_valid && rt->table_slots == S;
   if (same && (rt->table_types & mask) == mask) return KL_OK;
   const uint32_t want = mask | (same ? rt->table_types : 0u);
@@ -533,6 +552,7 @@ int retire(kl_runtime* rt) {
     rt->last.slot_wait_ns = R.wait_ns;
     rt->last.stage_wait_ns = R.stage_wait_ns;
     rt->last.plan_ns = R.plan_ns;
+    for (int c = 1; c < 4; ++c) rt->last.class_ctas[c] = R.cls_ctas[c];
     float ms = 0.f;
     rt->last.kernel_ns =
         cudaEventElapsedTime(&ms, rt->ev_k0, rt->ev_k1) == cudaSuccess ? (uint64_t)((double)ms * 1e6) : 0;
@@ -667,6 +687,7 @@ int serve_publish(kl_runtime* rt, TenantDev td, uint64_t footprint, kl_handle* o
   if (!rt->in_flight || (rt->kind != kServe && rt->kind != kServeBase)) return KL_ESTATE;  // the run has ended
   if (rt->kind == kServeBase && rt->s_joined) return KL_ESTATE;
   if (rt->kind == kServe && __atomic_load_n(&rt->sm_ctl[32], __ATOMIC_RELAXED)) return KL_ESTATE;  // stopping
+  if (rt->kind == kServe && tn::resource_class(td.type) != tn::kClassMain) return KL_EINVAL;
   if (rt->kind == kServe && !tn::in_plain_build(td.type) && !(rt->cfg.flags & KL_CFG_SERVE_TC)) return KL_EINVAL;
   if (rt->s_inflight >= rt->cap) return KL_EAGAIN;
   if (rt->cfg.mem_cap_bytes && rt->s_footprint + footprint > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
@@ -741,7 +762,7 @@ extern "C" int kl_tenant_shape_of(uint32_t type, const void* args, uint32_t args
   memset(out, 0, sizeof(*out));
   out->grid[0] = tn::stage_blocks(type, blob, 0);
   out->grid[1] = out->grid[2] = 1;
-  out->block[0] = KL_BLOCK_THREADS;
+  out->block[0] = tn::block_threads(type);
   out->block[1] = out->block[2] = 1;
   out->nstages = tn::nstages(type, blob);
   out->smem_bytes = tn::smem_bytes(type);
@@ -914,7 +935,7 @@ static int submit_impl(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out, 
   if (!rt || !d || !out) return KL_EINVAL;
   *out = 0;
   if (d->type >= KL_T_COUNT || !d->args || d->args_size != args_size_of(d->type)) return KL_EINVAL;
-  if (d->block[0] != KL_BLOCK_THREADS || d->block[1] != 1 || d->block[2] != 1) return KL_EINVAL;
+  if (d->block[0] != tn::block_threads(d->type) || d->block[1] != 1 || d->block[2] != 1) return KL_EINVAL;
   kl_tenant_shape sh;
   int rc = kl_tenant_shape_of(d->type, d->args, d->args_size, &sh);
   if (rc) return rc;
@@ -968,20 +989,32 @@ static int launch_locked(kl_runtime* rt) {
   const uint32_t n = (uint32_t)rt->pending.size();
   if (n == 0) return KL_OK;
   if (cudaSetDevice(rt->device) != cudaSuccess) return KL_ECUDA;
-  uint32_t mask = 0, smem = tn::kMinCtaSmem;
+  uint32_t mask = 0, smem = tn::kMinCtaSmem, cls_mask = 0;
   for (const Pending& p : rt->pending) {
+    const int c = tn::resource_class(p.td.type);
+    if (c != tn::kClassMain) {
+      cls_mask |= 1u << c;  // run by its resource-class kernel beside the co-scheduler
+      continue;
+    }
     mask |= 1u << p.td.type;
     smem = std::max(smem, tn::smem_bytes(p.td.type));  // dynamic shared memory of this run's CTAs
   }
+  const bool has_main = mask != 0u;
   // the smallest build that holds every type of the run (tn::run_block)
-  int build = (mask >> (KL_T_MATADD + 1)) != 0u ? tn::kBuildFull : tn::kBuildPlain;
+  int build = tn::kBuildPlain;
   bool all_light = true;
-  for (uint32_t t = 0; t < KL_T_COUNT; ++t)
-    if ((mask >> t) & 1u) all_light = all_light && tn::in_light_build(t);
-  if (all_light && (rt->cfg.flags & KL_CFG_LIGHT_BUILD) && rt->slots_light && !rt->table_override)
+  for (uint32_t t = 0; t < KL_T_MAIN_COUNT; ++t)
+    if ((mask >> t) & 1u) {
+      if (!tn::in_plain_build(t)) build = tn::kBuildFull;
+      all_light = all_light && tn::in_light_build(t);
+    }
+  if (all_light && !cls_mask && (rt->cfg.flags & KL_CFG_LIGHT_BUILD) && rt->slots_light && !rt->table_override)
     build = tn::kBuildLight;
-  const uint32_t S = build == tn::kBuildLight ? rt->slots_light : rt->slots;
-  int rc = ensure_table(rt, mask, S);
+  uint32_t S = build == tn::kBuildLight ? rt->slots_light : rt->slots;
+  // a resource-class CTA takes up to half an SM's registers: the co-scheduler
+  // keeps two slots per SM beside it
+  if (cls_mask && has_main) S = std::min<uint32_t>(S, 2u);
+  int rc = has_main && S >= 1 ? ensure_table(rt, mask, S) : KL_OK;
   if (rc) return rc;
   // device image: run state, tenants, the "plan first" phase
   RunDev& R = *rt->h_run;
@@ -1000,6 +1033,14 @@ static int launch_locked(kl_runtime* rt) {
   memcpy(R.cp, rt->cp, sizeof(R.cp));
   memcpy(R.slots_a, rt->slots_a, sizeof(R.slots_a));
   memcpy(R.allowed, rt->allowed, sizeof(R.allowed));
+  R.n_sm = rt->n_sm;
+  R.quota_exit = (cls_mask && has_main) ? 1u : 0u;
+  // resource classes present in the run, each run by its class kernel with
+  // two CTAs per SM (they take the room the co-scheduler's two slots leave)
+  int cls_list[tn::kNumClasses];
+  uint32_t ncls = 0;
+  for (int c = 1; c < tn::kNumClasses; ++c)
+    if ((cls_mask >> c) & 1u) cls_list[ncls++] = c;
   for (uint32_t i = 0; i < n; ++i) {
     TenantDev td = rt->pending[i].td;
     td.slice = clamp_slice(rt, td.slice, td.total);
@@ -1021,11 +1062,33 @@ static int launch_locked(kl_runtime* rt) {
   const CopySeg out[3] = {{rt->hd_tenants, rt->d_tenants, sizeof(TenantDev) * n},
                           {rt->hd_run, rt->d_run, sizeof(RunDev)},
                           {rt->hd_phases, rt->d_phases, sizeof(PhaseDev) * R.max_phases}};
+  // resource-class kernels run on side streams forked from the runtime stream
+  // after the image is in, and joined back before the image comes out
+  while (rt->side.size() < ncls) {
+    cudaStream_t q;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) return KL_ECUDA;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return KL_ECUDA;
+    rt->side.push_back(q);
+    rt->side_join.push_back(e);
+  }
+  static const int cls_type[tn::kNumClasses] = {-1, KL_T_BS255, KL_T_HIST1024, KL_T_GEMM_F32_BIG};
   rc = cuda_ok(cudaEventRecord(rt->ev_start, s));
   if (!rc && stage_copy(in, 3, s) != 0) rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k0, s));
-  if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, S, smem, build, s) != 0)
+  if (!rc && ncls) rc = cuda_ok(cudaEventRecord(rt->ev_fork, s));
+  // the co-scheduler first: its CTAs take their two slots on every SM before
+  // the class CTAs fill the rest
+  if (!rc && has_main &&
+      cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, S, smem, build, s, R.quota_exit ? rt->n_sm : 0u) != 0)
     rc = KL_ECUDA;
+  for (uint32_t q = 0; q < ncls && !rc; ++q) {
+    rc = cuda_ok(cudaStreamWaitEvent(rt->side[q], rt->ev_fork, 0));
+    if (!rc && class_launch(cls_type[cls_list[q]], rt->d_tenants, rt->d_run, 2u * rt->n_sm, rt->side[q]) != 0)
+      rc = KL_ECUDA;
+    if (!rc) rc = cuda_ok(cudaEventRecord(rt->side_join[q], rt->side[q]));
+  }
+  for (uint32_t q = 0; q < ncls && !rc; ++q) rc = cuda_ok(cudaStreamWaitEvent(s, rt->side_join[q], 0));
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
   if (!rc && stage_copy(out, 3, s) != 0) rc = KL_ECUDA;
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_done, s));
@@ -1152,6 +1215,7 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     RunDev& R = *rt->h_run;
     memset(&R, 0, sizeof(R));
     R.slots = rt->slots;
+    R.n_sm = rt->n_sm;
     R.max_phases = rt->s_phase_slots;
     R.n_types = KL_T_COUNT;
     R.wait_limit_ns = rt->cfg.device_wait_limit_ns;

@@ -60,6 +60,16 @@ constexpr int kTeaPerBlock = 512;        // 64-bit blocks (two per thread, one 1
 constexpr int kSadPerBlock = 256;        // SAD values (one per thread)
 constexpr int kStencilPerBlock = 256;    // consecutive points (x fastest) of a block
 constexpr int kMriqPerBlock = 256;       // k-samples (stage 0) or image points (stage 1)
+// Resource-heavy variants, each run by a resource-class kernel of its own
+constexpr int kBs255Threads = 128, kBs255PerThread = 32;
+constexpr int kBs255PerBlock = kBs255Threads * kBs255PerThread;  // 4096 options
+constexpr int kHist1024Threads = 1024;
+constexpr int kHist1024BytesPerBlock = kHist1024Threads * 128;  // 131072
+constexpr int kGbBM = 128, kGbBN = 128, kGbBK = 32, kGbStages = 3;
+constexpr int kGbAStride = kGbBK + 4;                      // row-major A tile rows, 16-byte aligned
+constexpr uint32_t kGbStageFloats = kGbBM * kGbAStride + kGbBK * kGbBN;
+constexpr uint32_t kGbSmem = kGbStages * kGbStageFloats * 4u;  // 3 x 32.5 KB = 97.5 KB
+constexpr int kTestmixPerBlock = 256;
 
 __host__ __device__ inline uint32_t bitonic_tile_log2(uint32_t L) {
   return L < (uint32_t)kBitonicTileLog2 ? L : (uint32_t)kBitonicTileLog2;
@@ -75,6 +85,7 @@ __host__ __device__ inline uint32_t bitonic_nstages(uint32_t L) {
 __host__ __device__ inline uint32_t nstages(uint32_t type, const void* a) {
   switch (type) {
     case KL_T_HIST256: return 2;
+    case KL_T_HIST1024: return 2;
     case KL_T_MRIQ: return 2;
     case KL_T_BITONIC: return bitonic_nstages(((const kl_args_bitonic*)a)->log2n);
     default: return 1;
@@ -123,6 +134,13 @@ __host__ __device__ inline uint32_t stage_blocks(uint32_t type, const void* a, u
       const kl_args_mriq* m = (const kl_args_mriq*)a;
       return s == 0 ? cdiv64(m->numK, kMriqPerBlock) : cdiv64(m->numX, kMriqPerBlock);
     }
+    case KL_T_TESTMIX: return cdiv64(((const kl_args_testmix*)a)->nthreads, kTestmixPerBlock);
+    case KL_T_BS255: return cdiv64(((const kl_args_blackscholes*)a)->n, kBs255PerBlock);
+    case KL_T_HIST1024: return s == 0 ? 1u : cdiv64(((const kl_args_hist256*)a)->n, kHist1024BytesPerBlock);
+    case KL_T_GEMM_F32_BIG: {
+      const kl_args_gemm_f32* g = (const kl_args_gemm_f32*)a;
+      return cdiv64(g->M, kGbBM) * cdiv64(g->N, kGbBN);
+    }
     default: return 0;
   }
 }
@@ -137,7 +155,7 @@ __host__ __device__ inline uint64_t total_blocks(uint32_t type, const void* a) {
 
 // Stage containing cumulative block g (g < total).
 __host__ __device__ inline Stage stage_of(uint32_t type, const void* a, uint32_t g) {
-  if (type == KL_T_HIST256) {
+  if (type == KL_T_HIST256 || type == KL_T_HIST1024) {
     if (g == 0) return Stage{0, 0, 1};
     return Stage{1, 1, 1 + stage_blocks(type, a, 1)};
   }
@@ -171,15 +189,30 @@ __host__ __device__ inline Stage stage_of(uint32_t type, const void* a, uint32_t
 //                blocks per kernel: a pair and its fill list leave most of 8
 //                slots per SM idle).
 enum : int { kBuildPlain = 0, kBuildFull = 1, kBuildLight = 2 };
-__host__ __device__ constexpr bool in_plain_build(uint32_t type) { return type <= KL_T_MATADD; }
+__host__ __device__ constexpr bool in_plain_build(uint32_t type) {
+  return type <= KL_T_MATADD || type == KL_T_TESTMIX;
+}
 __host__ __device__ constexpr bool in_light_build(uint32_t type) {
   return type == KL_T_GATHER || type == KL_T_BLACKSCHOLES || type == KL_T_SPMV_CSR || type == KL_T_TRIAD ||
-         type == KL_T_ESCAPE || type == KL_T_MATADD || type == KL_T_TEA || type == KL_T_STENCIL;
+         type == KL_T_ESCAPE || type == KL_T_MATADD || type == KL_T_TEA || type == KL_T_STENCIL ||
+         type == KL_T_TESTMIX;
 }
 __host__ __device__ constexpr bool in_build(int build, uint32_t type) {
-  return build == kBuildFull    ? type < KL_T_COUNT
+  return build == kBuildFull    ? type < KL_T_MAIN_COUNT
          : build == kBuildLight ? in_light_build(type)
                                 : in_plain_build(type);
+}
+// Resource classes: 0 = the co-scheduler's 256-thread, 64-register slots; the
+// heavy variants each run in a persistent kernel of their own (kl_cosched.cu,
+// class_kernel) with one CTA per SM beside two co-scheduler slots: each of
+// those CTAs takes at most half of the SM's 64 K registers.
+enum : int { kClassMain = 0, kClassBs255 = 1, kClassHist1024 = 2, kClassGemmBig = 3, kNumClasses = 4 };
+__host__ __device__ constexpr int resource_class(uint32_t type) {
+  return type == KL_T_BS255 ? kClassBs255 : type == KL_T_HIST1024 ? kClassHist1024
+                                          : type == KL_T_GEMM_F32_BIG ? kClassGemmBig : kClassMain;
+}
+__host__ __device__ constexpr uint32_t block_threads(uint32_t type) {
+  return type == KL_T_BS255 ? (uint32_t)kBs255Threads : type == KL_T_HIST1024 ? (uint32_t)kHist1024Threads : 256u;
 }
 
 __host__ __device__ constexpr uint32_t smem_bytes(uint32_t type) {
@@ -190,15 +223,17 @@ __host__ __device__ constexpr uint32_t smem_bytes(uint32_t type) {
     case KL_T_BITONIC: return ((1u << kBitonicTileLog2) + (1u << (kBitonicTileLog2 - 5))) * 4u;  // padded tile
     case KL_T_GEMM_BF16: return kBfSmem;                                          // 49.1 KB
     case KL_T_MRIQ: return 4u * kMriqPerBlock * 4u;                               // 4 KB k-sample chunk
+    case KL_T_HIST1024: return 256u * 32u * 4u;                                   // 32 KB
+    case KL_T_GEMM_F32_BIG: return kGbSmem;                                       // 97.5 KB
     default: return 0;
   }
 }
-constexpr uint32_t kMaxTenantSmem = kBfSmem;  // largest of the above (BF16 GEMM)
+constexpr uint32_t kMaxTenantSmem = kBfSmem;  // largest of the co-scheduler's types (BF16 GEMM)
 constexpr uint32_t kMaxLightSmem = 2048;       // the light build's types need at most 256 B (SpMV)
 constexpr uint32_t kMinCtaSmem = 2048;         // co-scheduler CTAs always have this much (re-plan scratch)
 static_assert(256u * 32u * 4u <= kMaxTenantSmem, "smem bound");
 __host__ __device__ constexpr bool light_smem_fits() {
-  for (uint32_t t = 0; t < KL_T_COUNT; ++t)
+  for (uint32_t t = 0; t < KL_T_MAIN_COUNT; ++t)
     if (in_light_build(t) && smem_bytes(t) > kMaxLightSmem) return false;
   return true;
 }
@@ -336,11 +371,8 @@ __device__ __forceinline__ void gather_block(const kl_args_gather& a, uint32_t v
 
 // ------------------------------------------------------------------ Black-Scholes
 
-__device__ __forceinline__ void blackscholes_block(const kl_args_blackscholes& a, uint32_t vb) {
-  const uint64_t i = (uint64_t)vb * kBsPerBlock + threadIdx.x;
-  if (i >= a.n) return;
-  float s = __ldcs(a.S + i), k = __ldcs(a.K + i), rr = __ldcs(a.r + i), vv = __ldcs(a.v + i),
-        tt = __ldcs(a.T + i);
+// One option by the written recipe (every operation separately rounded).
+__device__ __forceinline__ void bs_option(float s, float k, float rr, float vv, float tt, float& call, float& put) {
   float sqrtT = __fsqrt_rn(tt);
   float vsqrtT = __fmul_rn(vv, sqrtT);
   float q = __fdiv_rn(s, k);
@@ -359,12 +391,49 @@ __device__ __forceinline__ void blackscholes_block(const kl_args_blackscholes& a
   float kd = __fmul_rn(k, disc);
   float t1 = __fmul_rn(s, c1);
   float t2 = __fmul_rn(kd, c2);
-  __stcs(a.call + i, __fsub_rn(t1, t2));
+  call = __fsub_rn(t1, t2);
   float u2 = __fsub_rn(1.0f, c2);
   float u1 = __fsub_rn(1.0f, c1);
   float p1 = __fmul_rn(kd, u2);
   float p2 = __fmul_rn(s, u1);
-  __stcs(a.put + i, __fsub_rn(p1, p2));
+  put = __fsub_rn(p1, p2);
+}
+
+__device__ __forceinline__ void blackscholes_block(const kl_args_blackscholes& a, uint32_t vb) {
+  const uint64_t i = (uint64_t)vb * kBsPerBlock + threadIdx.x;
+  if (i >= a.n) return;
+  float c, p;
+  bs_option(__ldcs(a.S + i), __ldcs(a.K + i), __ldcs(a.r + i), __ldcs(a.v + i), __ldcs(a.T + i), c, p);
+  __stcs(a.call + i, c);
+  __stcs(a.put + i, p);
+}
+
+// Resource-heavy variant (128 threads): 32 options a thread, all inputs loaded
+// into registers before any is priced, option j of thread t at block offset
+// 128 j + t (coalesced per j). Same arithmetic per option as above.
+__device__ __forceinline__ void bs255_block(const kl_args_blackscholes& a, uint32_t vb) {
+  const uint64_t base = (uint64_t)vb * kBs255PerBlock + threadIdx.x;
+  float s[kBs255PerThread], k[kBs255PerThread], r[kBs255PerThread], v[kBs255PerThread], t[kBs255PerThread];
+#pragma unroll
+  for (int j = 0; j < kBs255PerThread; ++j) {
+    const uint64_t i = base + (uint64_t)j * kBs255Threads;
+    const bool ok = i < a.n;
+    s[j] = ok ? __ldcs(a.S + i) : 1.0f;
+    k[j] = ok ? __ldcs(a.K + i) : 1.0f;
+    r[j] = ok ? __ldcs(a.r + i) : 0.0f;
+    v[j] = ok ? __ldcs(a.v + i) : 1.0f;
+    t[j] = ok ? __ldcs(a.T + i) : 1.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < kBs255PerThread; ++j) {
+    const uint64_t i = base + (uint64_t)j * kBs255Threads;
+    float c, p;
+    bs_option(s[j], k[j], r[j], v[j], t[j], c, p);
+    if (i < a.n) {
+      __stcs(a.call + i, c);
+      __stcs(a.put + i, p);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ FP32 GEMM
@@ -458,6 +527,112 @@ __device__ __forceinline__ void gemm_f32_block(const kl_args_gemm_f32& a, uint32
             make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     }
   }
+}
+
+// Resource-heavy variant: one 128 x 128 tile of C per block of 256 threads,
+// K in steps of 32 through a three-stage cp.async ring of A (row-major rows,
+// padded) and B tiles (97.5 KB of shared memory). Thread (ty, tx) of 16 x 16
+// holds rows ty*4 + {0..3} and 64 + ty*4 + {0..3} and the same columns from
+// tx: 64 accumulators, each the ascending fused chain over k from +0 of the
+// definition (bit-identical to the oracle).
+__device__ __forceinline__ void gemm_big_block(const kl_args_gemm_f32& a, uint32_t vb, char* smem) {
+  float* sbase = reinterpret_cast<float*>(smem);
+  const uint32_t tilesN = (a.N + kGbBN - 1) / kGbBN;
+  const uint32_t m0 = (vb / tilesN) * kGbBM, n0 = (vb % tilesN) * kGbBN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const uint32_t ktiles = (a.K + kGbBK - 1) / kGbBK;
+  auto As = [&](int st) { return sbase + st * kGbStageFloats; };
+  auto Bs = [&](int st) { return sbase + st * kGbStageFloats + kGbBM * kGbAStride; };
+  auto load = [&](uint32_t kt, int st) {
+    // A: 128 rows x 8 chunks of 4 floats; B: 32 rows x 32 chunks; 4 of each a thread
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = tid + u * 256;
+      const int ar = c >> 3, ak = (c & 7) * 4;
+      const uint32_t gm = m0 + ar, gk = kt * kGbBK + ak;
+      const bool aok = gm < a.M && gk < a.K;
+      cp_async16(As(st) + ar * kGbAStride + ak, aok ? a.A + (uint64_t)gm * a.K + gk : a.A, aok ? 16 : 0);
+      const int br = c >> 5, bn = (c & 31) * 4;
+      const uint32_t gk2 = kt * kGbBK + br, gn = n0 + bn;
+      const bool bok = gk2 < a.K && gn < a.N;
+      cp_async16(Bs(st) + br * kGbBN + bn, bok ? a.B + (uint64_t)gk2 * a.N + gn : a.B, bok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  load(0, 0);
+  if (ktiles > 1) load(1, 1);
+  for (uint32_t kt = 0; kt < ktiles; ++kt) {
+    const int st = kt % kGbStages;
+    if (kt + 1 < ktiles)
+      cp_async_wait<1>();
+    else
+      cp_async_wait<0>();
+    __syncthreads();  // stage kt landed for everyone; stage kt-1 is no longer read
+    if (kt + 2 < ktiles) load(kt + 2, (kt + 2) % kGbStages);
+    const float* A0 = As(st) + (ty * 4) * kGbAStride;
+    const float* A1 = As(st) + (64 + ty * 4) * kGbAStride;
+    const float* B0 = Bs(st) + tx * 4;
+#pragma unroll
+    for (int k2 = 0; k2 < kGbBK; k2 += 2) {
+      float2 ar[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ar[i] = *reinterpret_cast<const float2*>(A0 + i * kGbAStride + k2);
+        ar[4 + i] = *reinterpret_cast<const float2*>(A1 + i * kGbAStride + k2);
+      }
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const float4 b0 = *reinterpret_cast<const float4*>(B0 + (k2 + kk) * kGbBN);
+        const float4 b1 = *reinterpret_cast<const float4*>(B0 + (k2 + kk) * kGbBN + 64);
+        const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float av = kk == 0 ? ar[i].x : ar[i].y;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = __fmaf_rn(av, br[j], acc[i][j]);
+        }
+      }
+    }
+  }
+  __syncthreads();  // the next block reuses the ring
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (gm >= a.M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t gn = n0 + h * 64 + tx * 4;
+      if (gn < a.N)
+        *reinterpret_cast<float4*>(a.C + (uint64_t)gm * a.N + gn) =
+            make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ testing kernel (Section 4.3)
+// Thread g: `iters` rounds of `mem` streaming loads (consecutive threads read
+// consecutive words; each round a fresh stretch of the input) added to acc,
+// then `alu` dependent fused multiply-adds acc = c1 acc + c2. The ratio of the
+// two sets the kernel's pipeline and memory-bandwidth utilisation.
+__device__ __forceinline__ void testmix_block(const kl_args_testmix& a, uint32_t vb) {
+  const uint32_t g = vb * kTestmixPerBlock + threadIdx.x;
+  if (g >= a.nthreads) return;
+  const uint32_t mask = a.n_in - 1u;
+  float acc = 0.0f;
+  uint32_t idx = g & mask;
+  for (uint32_t it = 0; it < a.iters; ++it) {
+    for (uint32_t m = 0; m < a.mem; ++m) {
+      acc = __fadd_rn(acc, __ldcs(a.in + idx));
+      idx = (idx + a.nthreads) & mask;
+    }
+    for (uint32_t q = 0; q < a.alu; ++q) acc = __fmaf_rn(acc, a.c1, a.c2);
+  }
+  a.out[g] = acc;
 }
 
 // ------------------------------------------------------------------ CSR SpMV
@@ -623,6 +798,50 @@ __device__ __forceinline__ void hist256_block(const kl_args_hist256& a, uint32_t
 #pragma unroll 8
   for (uint32_t c = 0; c < 32; ++c) sum += sh[threadIdx.x << 5 | ((c + lane) & 31)];
   if (sum) atomicAdd(a.hist + threadIdx.x, sum);
+}
+
+// Resource-heavy variant: 1024-thread blocks of 131072 bytes (eight 16-byte
+// loads a thread), the same 32 lane-private copies of the 256 bins in shared
+// memory (each shared by the 32 warps), then per bin one global add.
+__device__ __forceinline__ void hist1024_block(const kl_args_hist256& a, uint32_t stage, uint32_t vb, char* smem) {
+  if (stage == 0) {
+    if (threadIdx.x < 256) a.hist[threadIdx.x] = 0u;
+    return;
+  }
+  uint32_t* sh = reinterpret_cast<uint32_t*>(smem);  // [256][32]
+  const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 0; w < 2; ++w)
+    reinterpret_cast<uint4*>(sh)[w * kHist1024Threads + threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  const uint64_t base = (uint64_t)vb * kHist1024BytesPerBlock;
+  if (base + kHist1024BytesPerBlock <= a.n) {
+    uint4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      v[u] = __ldcs(reinterpret_cast<const uint4*>(a.data + base + ((uint64_t)u * kHist1024Threads + threadIdx.x) * 16));
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const uint32_t w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        atomicAdd(sh + (((w4[q] >> 0) & 0xffu) << 5 | lane), 1u);
+        atomicAdd(sh + (((w4[q] >> 8) & 0xffu) << 5 | lane), 1u);
+        atomicAdd(sh + (((w4[q] >> 16) & 0xffu) << 5 | lane), 1u);
+        atomicAdd(sh + ((w4[q] >> 24) << 5 | lane), 1u);
+      }
+    }
+  } else {
+    for (uint64_t i = base + threadIdx.x; i < a.n && i < base + kHist1024BytesPerBlock; i += kHist1024Threads)
+      atomicAdd(sh + ((uint32_t)a.data[i] << 5 | lane), 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (uint32_t c = 0; c < 32; ++c) sum += sh[threadIdx.x << 5 | ((c + lane) & 31)];
+    if (sum) atomicAdd(a.hist + threadIdx.x, sum);
+  }
 }
 
 // ------------------------------------------------------------------ escape-time
@@ -1437,6 +1656,9 @@ __device__ __forceinline__ void run_block(uint32_t type, const void* args, const
     case KL_T_MRIQ:
       if constexpr (in_build(BUILD, KL_T_MRIQ)) mriq_block(load_args<kl_args_mriq>(args), st.s, vb, smem);
       break;
+    case KL_T_TESTMIX:
+      if constexpr (in_build(BUILD, KL_T_TESTMIX)) testmix_block(load_args<kl_args_testmix>(args), vb);
+      break;
     default: break;
   }
 }
@@ -1533,6 +1755,11 @@ __device__ __forceinline__ void run_slice(uint32_t type, const void* args, const
       if constexpr (in_build(BUILD, KL_T_MRIQ))
         slice_loop<kl_args_mriq, true>(
             args, v0, v1, [&](const kl_args_mriq& a, uint32_t vb) { mriq_block(a, s, vb, smem); });
+      break;
+    case KL_T_TESTMIX:
+      if constexpr (in_build(BUILD, KL_T_TESTMIX))
+        slice_loop<kl_args_testmix, false>(args, v0, v1,
+                                           [&](const kl_args_testmix& a, uint32_t vb) { testmix_block(a, vb); });
       break;
     default: break;
   }

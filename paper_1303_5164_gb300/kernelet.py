@@ -22,10 +22,12 @@ KL_PENDING, KL_RUNNING, KL_DONE, KL_ERROR = 0, 1, 2, 3
 
 (KL_T_GATHER, KL_T_BLACKSCHOLES, KL_T_GEMM_F32, KL_T_SPMV_CSR, KL_T_PCHASE, KL_T_TRIAD,
  KL_T_HIST256, KL_T_ESCAPE, KL_T_BITONIC, KL_T_MATADD, KL_T_GEMM_BF16, KL_T_TEA, KL_T_SAD, KL_T_STENCIL,
- KL_T_MRIQ) = range(15)
-KL_T_COUNT = 15
+ KL_T_MRIQ, KL_T_TESTMIX, KL_T_BS255, KL_T_HIST1024, KL_T_GEMM_F32_BIG) = range(19)
+KL_T_COUNT = 19
+KL_T_MAIN_COUNT = 16
 TYPE_NAMES = ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256",
-              "escape", "bitonic", "matadd", "gemm_bf16", "tea", "sad", "stencil", "mriq"]
+              "escape", "bitonic", "matadd", "gemm_bf16", "tea", "sad", "stencil", "mriq", "testmix",
+              "bs255", "hist1024", "gemm_f32_big"]
 KL_RATIO_BALANCED, KL_RATIO_MAX_CP, KL_RATIO_FIXED = 0, 1, 2
 KL_BASE_SERIAL, KL_BASE_MULTISTREAM, KL_SERVE_COSCHED = 0, 1, 2
 KL_CFG_BACKFILL = 1
@@ -76,6 +78,11 @@ class kl_args_escape(C.Structure):
                 ("x0", F32), ("y0", F32), ("dx", F32), ("dy", F32)]
 
 
+class kl_args_testmix(C.Structure):
+    _fields_ = [("in_", P), ("out", P), ("n_in", U32), ("nthreads", U32), ("iters", U32), ("mem", U32),
+                ("alu", U32), ("pad", U32), ("c1", F32), ("c2", F32)]
+
+
 class kl_args_bitonic(C.Structure):
     _fields_ = [("in_", P), ("out", P), ("log2n", U32), ("pad", U32)]
 
@@ -109,7 +116,8 @@ class kl_args_mriq(C.Structure):
 
 ARGS_TYPES = [kl_args_gather, kl_args_blackscholes, kl_args_gemm_f32, kl_args_spmv_csr,
               kl_args_pchase, kl_args_triad, kl_args_hist256, kl_args_escape, kl_args_bitonic,
-              kl_args_matadd, kl_args_gemm_bf16, kl_args_tea, kl_args_sad, kl_args_stencil, kl_args_mriq]
+              kl_args_matadd, kl_args_gemm_bf16, kl_args_tea, kl_args_sad, kl_args_stencil, kl_args_mriq,
+              kl_args_testmix]
 
 
 class kl_tenant_shape(C.Structure):
@@ -157,7 +165,7 @@ class kl_run_stats(C.Structure):
     _fields_ = [("n_tenants", U32), ("n_phases", U32), ("error", I32), ("slots_per_sm", U32),
                 ("grid_ctas", U32), ("pad", U32), ("t_launch_ns", U64), ("t_end_ns", U64),
                 ("kernel_ns", U64), ("run_ns", U64), ("slot_wait_ns", U64), ("stage_wait_ns", U64),
-                ("plan_ns", U64)]
+                ("plan_ns", U64), ("class_ctas", U32 * 4)]
 
 
 class KLError(RuntimeError):
@@ -209,7 +217,7 @@ SIGNATURES = [
                                  C.POINTER(I32)]),
 ]
 KL_NOALLOC_MAX_TENANTS = 64
-KL_NOALLOC_SCRATCH_BYTES = 95232
+KL_NOALLOC_SCRATCH_BYTES = 97536
 
 
 def lib_path() -> str:
@@ -298,7 +306,7 @@ def make_desc(type_: int, args, slice_blocks: int = 0, footprint: int = 0) -> kl
     d = kl_kernel_desc()
     d.type = type_
     d.grid[:] = list(sh.grid)
-    d.block[:] = [KL_BLOCK_THREADS, 1, 1]
+    d.block[:] = list(sh.block)
     d.smem_bytes = sh.smem_bytes
     d.slice_blocks = slice_blocks
     d.args = C.cast(C.byref(args), P)
@@ -340,7 +348,7 @@ class Runtime:
         d = kl_kernel_desc()
         d.type = type_
         d.grid[:] = list(sh.grid)
-        d.block[:] = [KL_BLOCK_THREADS, 1, 1]
+        d.block[:] = list(sh.block)
         d.smem_bytes = sh.smem_bytes
         d.slice_blocks = slice_blocks
         d.args = C.cast(C.byref(args), P)

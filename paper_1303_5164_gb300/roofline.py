@@ -14,7 +14,14 @@ BS_FLOPS_PER_OPTION = 93
 ESCAPE_FLOPS_PER_ITER = 7
 
 
+# the resource-heavy variants do their base kernel's work
+BASE = {"bs255": "blackscholes", "hist1024": "hist256", "gemm_f32_big": "gemm_f32"}
+
+
 def algo_bytes(name: str, inp: dict) -> int:
+    name = BASE.get(name, name)
+    if name == "testmix":
+        return 4 * inp["iters"] * inp["mem"] * inp["nthreads"] + 4 * inp["nthreads"]
     if name == "gather":
         return 12 * inp["n"]
     if name == "blackscholes":
@@ -49,6 +56,10 @@ def algo_bytes(name: str, inp: dict) -> int:
     raise ValueError(name)
 
 
+def _base(name):
+    return BASE.get(name, name)
+
+
 def tensor_flops(name: str, inp: dict) -> int:
     """Operations on the tensor cores (the BF16 GEMM: 2 M N K)."""
     if name == "gemm_bf16":
@@ -58,6 +69,9 @@ def tensor_flops(name: str, inp: dict) -> int:
 
 def fp32_flops(name: str, inp: dict, escape_iters: int | None = None) -> int:
     """binary32 operations on the FP32 pipe (integer tenants: 0)."""
+    name = _base(name)
+    if name == "testmix":
+        return inp["iters"] * (inp["mem"] + 2 * inp["alu"]) * inp["nthreads"]
     if name == "gemm_f32":
         return 2 * inp["M"] * inp["N"] * inp["K"]
     if name == "blackscholes":
@@ -90,6 +104,9 @@ def lane_ops(name: str, inp: dict, escape_iters: int | None = None) -> int:
     lanes of an SM. Set against numSM x 128 x f_SM slots per second this is
     the issue-bound time of tenants that are neither HBM- nor FFMA-bound
     (Black-Scholes, escape-time, the bitonic passes, TEA)."""
+    name = _base(name)
+    if name == "testmix":
+        return inp["iters"] * (inp["mem"] + inp["alu"]) * inp["nthreads"]
     if name == "gemm_f32":
         return inp["M"] * inp["N"] * inp["K"]
     if name == "blackscholes":

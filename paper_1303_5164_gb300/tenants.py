@@ -53,7 +53,8 @@ class Tenant:
         out = {}
         for k in self.outputs:
             a = self.bufs[k].cpu().numpy()
-            if k in ("hist", "count", "out", "sad") and self.name in ("hist256", "escape", "bitonic", "tea", "sad"):
+            if k in ("hist", "count", "out", "sad") and self.name in ("hist256", "hist1024", "escape", "bitonic",
+                                                                        "tea", "sad"):
                 a = a.view(np.uint32)
             out[k] = a
         return out
@@ -83,14 +84,20 @@ def make(name: str, inp: dict, device="cuda") -> Tenant:
         b["out"] = _empty(inp["n"], torch.int32, device)
         args = K.kl_args_gather(_ptr(b["a"]), _ptr(b["idx"]), _ptr(b["out"]), inp["n"])
         outs = ["out"]
-    elif name == "blackscholes":
+    elif name == "testmix":
+        b["in_"] = _dev(inp["data"], device)
+        b["out"] = _empty(inp["nthreads"], torch.float32, device)
+        args = K.kl_args_testmix(_ptr(b["in_"]), _ptr(b["out"]), inp["n_in"], inp["nthreads"], inp["iters"],
+                                 inp["mem"], inp["alu"], 0, float(inp["c1"]), float(inp["c2"]))
+        outs = ["out"]
+    elif name in ("blackscholes", "bs255"):
         for k in "SKrvT":
             b[k] = _dev(inp[k], device)
         b["call"] = _empty(inp["n"], torch.float32, device)
         b["put"] = _empty(inp["n"], torch.float32, device)
         args = K.kl_args_blackscholes(*[_ptr(b[k]) for k in ["S", "K", "r", "v", "T", "call", "put"]], inp["n"])
         outs = ["call", "put"]
-    elif name == "gemm_f32":
+    elif name in ("gemm_f32", "gemm_f32_big"):
         b["A"], b["B"] = _dev(inp["A"], device), _dev(inp["B"], device)
         b["C"] = _empty((inp["M"], inp["N"]), torch.float32, device)
         args = K.kl_args_gemm_f32(_ptr(b["A"]), _ptr(b["B"]), _ptr(b["C"]), inp["M"], inp["N"], inp["K"], 0)
@@ -113,7 +120,7 @@ def make(name: str, inp: dict, device="cuda") -> Tenant:
         b["a"] = _empty(inp["n"], torch.float32, device)
         args = K.kl_args_triad(_ptr(b["b"]), _ptr(b["c"]), _ptr(b["a"]), float(inp["s"]), 0, inp["n"])
         outs = ["a"]
-    elif name == "hist256":
+    elif name in ("hist256", "hist1024"):
         b["data"] = _dev(inp["data"], device)
         b["hist"] = _empty(256, torch.int32, device)
         args = K.kl_args_hist256(_ptr(b["data"]), _ptr(b["hist"]), inp["n"])

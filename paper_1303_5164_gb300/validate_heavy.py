@@ -1,7 +1,10 @@
-"""Resource-heavy co-scheduling on the GPU: the BF16 tensor-core GEMM 4096^3
+"""Resource-heavy co-scheduling on the GPU: the FP32 GEMM 4096^3 with 128 x 128
+tiles in 96 KB of shared memory per block and its BF16 tensor-core variant
 (49 KB of shared memory and 64 TMEM columns per block), Black-Scholes 4 Mi
-options, the 256-bin histogram of 64 Mi bytes and a pointer chase over a
-1 GiB random cycle (65,536 chasers x 256 hops).
+options at up to 255 registers per thread, the 256-bin histogram of 64 Mi
+bytes with 1024-thread blocks, and a pointer chase over a 1 GiB random cycle
+(65,536 chasers x 256 hops). The FP32 GEMM, Black-Scholes and histogram
+variants run in resource-class kernels beside the co-scheduler.
 
 Each kernel runs alone in the co-scheduler, then every pair at the model's
 balanced slot split (Eq. executiontime), then all four submitted together.
@@ -26,9 +29,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HEAVY = {
-    "gemm_bf16": dict(M=4096, N=4096, K=4096),
-    "blackscholes": dict(n=4 * 1024 * 1024),
-    "hist256": dict(n=64 * 1024 * 1024),
+    "gemm_f32_big": dict(M=4096, N=4096, K=4096),   # 96 KB of shared memory per block
+    "gemm_bf16": dict(M=4096, N=4096, K=4096),      # its tensor-core variant (TMA, tcgen05, TMEM)
+    "bs255": dict(n=4 * 1024 * 1024),               # up to 255 registers per thread
+    "hist1024": dict(n=64 * 1024 * 1024),           # 1024 threads per block
     "pchase": dict(N=1 << 28, nchasers=65536, hops=256),
 }
 
@@ -99,6 +103,8 @@ def run(out_path, reps=3):
                 if got[k].tobytes() != v.tobytes():
                     raise AssertionError(f"{nm}.{k}: co-scheduled output differs from the plain launch")
 
+    class_ctas = {}
+
     def go(sel, base=None, ns=4):
         r2 = heavy_runtime(K, cfg, mp, profs)
         best = None
@@ -112,38 +118,49 @@ def run(out_path, reps=3):
                 r2.launch_baseline(base, ns)
             assert r2.drain() == 0
             check(sel)
-            ker = r2.run_stats().kernel_ns / 1e3
+            rs = r2.run_stats()
+            ker = rs.kernel_ns / 1e3
             if best is None or ker < best[1]:
                 best = (r2.phases() if base is None else [], ker)
+                class_ctas[tuple(sel) + (base,)] = list(rs.class_ctas)[1:]
         r2.close()
         return best
 
+    main_class = {nm: K.TYPE_NAMES.index(nm) < K.KL_T_MAIN_COUNT for nm in names}
     for nm in names:
         ph, ker = go([nm])
-        (ipc, _), dur = _phase_ipc(ph, 1, [tens[nm]], profs, mp)
-        w = max(1, int(round(S * 8 / 4)))
-        pred = K.model_ipc(mp, [profs[tens[nm].type]], [w], 3)[0] if profs[tens[nm].type].valid else None
-        res["solo"][nm] = {"kernel_us": ker, "ipc_measured": ipc, "ipc_predicted": pred}
-        print("solo", nm, res["solo"][nm], flush=True)
+        entry = {"kernel_us": ker, "resource_class_kernel": not main_class[nm],
+                 "class_ctas_working": class_ctas.get((nm, None))}
+        if main_class[nm] and len(ph) > 2:
+            (ipc, _), dur = _phase_ipc(ph, 1, [tens[nm]], profs, mp)
+            w = max(1, int(round(S * 8 / 4)))
+            entry["ipc_measured"] = ipc
+            entry["ipc_predicted"] = (K.model_ipc(mp, [profs[tens[nm].type]], [w], 3)[0]
+                                      if profs[tens[nm].type].valid else None)
+        res["solo"][nm] = entry
+        print("solo", nm, entry, flush=True)
     for a, b in itertools.combinations(names, 2):
         ph, ker = go([a, b])
-        (ca, cb), dur = _phase_ipc(ph, 1, [tens[a], tens[b]], profs, mp)
-        sa = ph[1].slots_a
-        pa = pb = cp = None
-        if profs[tens[a].type].valid and profs[tens[b].type].valid:
-            pr = K.model_pair(mp, profs[tens[a].type], profs[tens[b].type], S, 3)
-            pa, pb, cp = pr["cipc_a"][sa - 1], pr["cipc_b"][sa - 1], pr["cp"][sa - 1]
         serial = res["solo"][a]["kernel_us"] + res["solo"][b]["kernel_us"]
-        res["pairs"][f"{a}+{b}"] = {"slots_a": sa, "kernel_us": ker, "solo_sum_us": serial,
-                                    "cipc_measured": [ca, cb], "cipc_predicted": [pa, pb], "cp_predicted": cp,
-                                    "first_phase_us": dur}
-        print("pair", a, b, json.dumps(res["pairs"][f"{a}+{b}"]), flush=True)
+        entry = {"kernel_us": ker, "solo_sum_us": serial, "class_ctas_working": class_ctas.get((a, b, None))}
+        if main_class[a] and main_class[b] and len(ph) > 2:
+            # both in the co-scheduler's slots: the model's pair prediction
+            (ca, cb), dur = _phase_ipc(ph, 1, [tens[a], tens[b]], profs, mp)
+            sa = ph[1].slots_a
+            pa = pb = cp = None
+            if profs[tens[a].type].valid and profs[tens[b].type].valid and 1 <= sa < S:
+                pr = K.model_pair(mp, profs[tens[a].type], profs[tens[b].type], S, 3)
+                pa, pb, cp = pr["cipc_a"][sa - 1], pr["cipc_b"][sa - 1], pr["cp"][sa - 1]
+            entry.update(slots_a=sa, cipc_measured=[ca, cb], cipc_predicted=[pa, pb], cp_predicted=cp,
+                         first_phase_us=dur)
+        res["pairs"][f"{a}+{b}"] = entry
+        print("pair", a, b, json.dumps(entry), flush=True)
     _, ker4 = go(names)
-    _, ms4 = go(names, K.KL_BASE_MULTISTREAM, 4)
+    _, ms4 = go(names, K.KL_BASE_MULTISTREAM, len(names))
     _, se4 = go(names, K.KL_BASE_SERIAL, 1)
-    res["four_way"] = {"cosched_us": ker4, "multistream4_us": ms4, "serial_us": se4,
-                       "speedup_vs_multistream": ms4 / ker4, "speedup_vs_serial": se4 / ker4}
-    print("four", json.dumps(res["four_way"]), flush=True)
+    res["all"] = {"kernels": names, "cosched_us": ker4, f"multistream{len(names)}_us": ms4, "serial_us": se4,
+                  "speedup_vs_multistream": ms4 / ker4, "speedup_vs_serial": se4 / ker4}
+    print("all", json.dumps(res["all"]), flush=True)
     with open(out_path, "w") as f:
         json.dump(res, f, indent=1)
 

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(K):
 
 def test_errors_without_gpu(K):
     L = K.lib()
-    assert L.kl_abi_version() == 1
+    assert L.kl_abi_version() == 2
     assert L.kl_strerror(K.KL_EINVAL) == b"invalid argument"
     out = C.c_void_p()
     cfg = K.config_default()

@@ -28,6 +28,12 @@ CASES = {
     "sad": dict(width=64, height=36, range=3),                  # 7056 values: 28 blocks, ragged
     "stencil": dict(nx=300, ny=17, nz=9),                       # 45,900 points: 180 blocks, the last ragged
     "mriq": dict(numK=300, numX=1000),                          # two sample chunks, ragged point block
+    # the Section 4.3 testing kernel: 3 blocks and a ragged tail, 14 rounds of 2 loads and 7 fused steps
+    "testmix": dict(log2_in=16, nthreads=3 * 256 + 5, iters=14, mem=2, alu=7),
+    # resource-heavy variants (resource-class kernels beside the co-scheduler)
+    "bs255": dict(n=3 * 4096 + 1001),                          # 4 blocks of 4096 options, ragged
+    "hist1024": dict(n=3 * 131072 + 5),                         # 4 counting blocks, ragged
+    "gemm_f32_big": dict(M=300, N=260, K=100),                  # 3 x 3 tiles of 128 x 128, ragged
 }
 
 

@@ -396,3 +396,29 @@ def test_mriq_against_binary64(oracle_tenants):
     bound = (pm64 * (6 * u * 2 * np.pi * scale + 8 * u + 6e-8 * (4 + np.abs(ang) / 8))).sum(axis=1) \
         + inp["numK"] * u * pm64.sum()
     assert np.all(np.abs(qr - qr64) <= bound) and np.all(np.abs(qi - qi64) <= bound)
+
+
+def test_testmix_index_sequence_sums_and_recurrence(oracle_tenants):
+    # Section 4.3 testing kernel. Small-integer inputs with c1 = 1, c2 = 0 give
+    # exact sums: each thread's total over its index sequence (g + j nthreads)
+    # mod n_in, j = 0 .. iters*mem - 1, computed here by numpy fancy indexing
+    rng = np.random.default_rng(4)
+    n_in, nth, iters, mem = 1 << 10, 300, 7, 3
+    data = rng.integers(-3, 4, n_in).astype(np.float32)
+    inp = dict(data=data, n_in=n_in, nthreads=nth, iters=iters, mem=mem, alu=5, c1=np.float32(1.0),
+               c2=np.float32(0.0))
+    j = np.arange(iters * mem)
+    idx = (np.arange(nth)[:, None] + j[None, :] * nth) % n_in
+    assert np.array_equal(oracle_tenants.testmix(inp), data[idx].astype(np.int64).sum(axis=1).astype(np.float32))
+    # no loads: iters*alu steps of acc = acc*1 + 1 from 0 count exactly
+    inp.update(mem=0, alu=11, c2=np.float32(1.0))
+    assert np.all(oracle_tenants.testmix(inp) == np.float32(iters * 11))
+    # one load then acc = 0.5 acc (exact scaling) each round: brute force in
+    # binary32 arithmetic round by round
+    d = rng.standard_normal(n_in).astype(np.float32)
+    inp = dict(data=d, n_in=n_in, nthreads=nth, iters=9, mem=1, alu=1, c1=np.float32(0.5), c2=np.float32(0.0))
+    acc = np.zeros(nth, np.float32)
+    for i in range(9):
+        acc = (acc + d[(np.arange(nth) + i * nth) % n_in]).astype(np.float32)
+        acc = (acc * np.float32(0.5)).astype(np.float32)
+    assert np.array_equal(oracle_tenants.testmix(inp), acc)

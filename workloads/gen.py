@@ -273,10 +273,21 @@ def gen_matadd(cs: int, ti: int, n: int = 256) -> dict:
                 b=normal_f32(stream_seed(cs, ti, "b"), n * n).reshape(n, n), n=n)
 
 
+def gen_testmix(cs: int, ti: int, log2_in: int, nthreads: int, iters: int, mem: int, alu: int,
+                c1: float = 0.999, c2: float = 0.001) -> dict:
+    """Input of the tunable testing kernel: 2^log2_in values N(0,1) and the
+    loop counts and coefficients that set its memory / arithmetic mix."""
+    n_in = 1 << log2_in
+    return dict(data=normal_f32(stream_seed(cs, ti, "in"), n_in), n_in=n_in, nthreads=nthreads, iters=iters,
+                mem=mem, alu=alu, c1=np.float32(c1), c2=np.float32(c2))
+
+
 def gen_tenant(name: str, cs: int, ti: int, **size) -> dict:
+    # the resource-heavy variants take the inputs of the kernel they vary
     fn = {"gather": gen_gather, "blackscholes": gen_blackscholes,
           "gemm_f32": gen_gemm_f32, "spmv_csr": gen_spmv_csr, "pchase": gen_pchase,
           "triad": gen_triad, "hist256": gen_hist256, "escape": gen_escape,
           "bitonic": gen_bitonic, "matadd": gen_matadd, "gemm_bf16": gen_gemm_bf16, "tea": gen_tea,
-          "sad": gen_sad, "stencil": gen_stencil, "mriq": gen_mriq}[name]
+          "sad": gen_sad, "stencil": gen_stencil, "mriq": gen_mriq, "testmix": gen_testmix,
+          "bs255": gen_blackscholes, "hist1024": gen_hist256, "gemm_f32_big": gen_gemm_f32}[name]
     return fn(cs, ti, **size)
