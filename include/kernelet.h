@@ -319,6 +319,12 @@ typedef enum {
                                still has blocks to hand out, so kernels with
                                fewer slices than the GPU has slots do not leave
                                slots idle; default on */
+#define KL_CFG_PHASE_MODEL 512u /* with the chain lane: the planner scores each pair
+                               as the phase the device runs, the pair plus the
+                               chain lane's kernel (the multi-stage type with
+                               the most blocks pending), with the three-kernel
+                               chain of kl_model_phase, at the pair's split that
+                               maximises that phase's CP; off by default */
 #define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their
@@ -628,6 +634,17 @@ int kl_model_pair(const kl_model_params* gp, const kl_profile* pa, const kl_prof
                   uint32_t slots, uint32_t model_states, uint32_t policy, uint32_t fixed_a,
                   double* cipc_a, double* cipc_b, double* cp, double* dT, double* solo_ipc,
                   uint32_t* best_a);
+
+/* A phase of n kernels (1..4) sharing every SM, kernel k on slots[k] of the
+ * total_slots slots per SM (Section 2.2: a co-schedule of n >= 1 slices;
+ * Section 4.4: the heterogeneous model handles more than two kernels; the
+ * co-scheduler's phases run a pair plus the chain lane's kernel):
+ * cipc_out[k] = concurrent IPC per SM, solo_out[k] = IPC alone at
+ * total_slots, *cp_out = CP by Eq. cp with n terms. Host arrays of n entries.
+ * KL_EINVAL on bad sizes or sum(slots) > total_slots. */
+int kl_model_phase(const kl_model_params* gp, const kl_profile* profiles, const uint32_t* slots, uint32_t n,
+                   uint32_t total_slots, uint32_t model_states, double* cipc_out, double* solo_out,
+                   double* cp_out);
 
 /* Greedy plan (Algorithm 1) of n kernels with types[i] and blocks[i] thread
  * blocks, all pending at time 0, simulated with the model's rates. Writes up

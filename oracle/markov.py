@@ -232,6 +232,22 @@ class PairEval:
     dT: float
 
 
+def phase_cp(profiles, slots, total_slots: int, gpu: GPUParams, three_state: bool = False):
+    """A phase of n kernels sharing the SM, kernel k on slots[k] block slots
+    (Section 2.2: a co-schedule of n slices; Section 4.4: the heterogeneous
+    chain of n kernels): per-kernel concurrent IPC per SM, solo IPC per SM at
+    `total_slots` (full occupancy), and CP by Eq. cp over the n kernels.
+    Kernels with no slot contribute nothing to CP."""
+    S = gpu.n_sched
+    w = [warps_on_virtual_sm(b, p.warps_per_block, S) for p, b in zip(profiles, slots)]
+    conc = model_ipc(profiles, w, gpu, three_state)[0]
+    cipc = [c * S for c in conc]
+    solo = [homogeneous_ipc(p, warps_on_virtual_sm(total_slots, p.warps_per_block, S), gpu, three_state) * S
+            for p in profiles]
+    terms = [c / s for c, s in zip(cipc, solo) if s > 0.0]
+    return cipc, solo, (1.0 - 1.0 / sum(terms)) if sum(terms) > 0.0 else 0.0
+
+
 def evaluate_pair(pA: KernelProfile, pB: KernelProfile, slots: int, gpu: GPUParams,
                   three_state: bool = False):
     """Every feasible slot split (bA + bB = slots, both >= 1) of the per-SM

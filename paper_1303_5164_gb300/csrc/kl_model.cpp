@@ -276,6 +276,38 @@ int pair(const kl_model_params& g, const kl_profile& pa, const kl_profile& pb, u
   return KL_OK;
 }
 
+// A phase of n kernels sharing each SM, kernel k on slots[k] of its slots
+// (Section 2.2: a co-schedule runs n >= 1 slices at once; the heterogeneous
+// chain of Section 4.4 extends to more than two kernels): the concurrent IPC
+// per SM of each, its solo IPC at `total` slots (full occupancy), and CP by
+// Eq. cp with n terms. A kernel with no slot has IPC 0 and adds nothing.
+int phase(const kl_model_params& g, const kl_profile* const* pp, const uint32_t* slots, int n, uint32_t total,
+          int states, double* cipc, double* solo, double* cpv) {
+  if (n < 1 || n > 4 || total < 1) return KL_EINVAL;
+  int w[4];
+  uint32_t used = 0;
+  for (int k = 0; k < n; ++k) {
+    w[k] = warps_on_vsm(slots[k], pp[k]->warps_per_block, g.n_sched);
+    used += slots[k];
+  }
+  if (used > total) return KL_EINVAL;
+  double o[4];
+  int rc = ipc(g, pp, w, n, states, o);
+  if (rc) return rc;
+  double sum = 0.0;
+  for (int k = 0; k < n; ++k) {
+    int ws = warps_on_vsm(total, pp[k]->warps_per_block, g.n_sched);
+    double v;
+    rc = ipc(g, pp + k, &ws, 1, states, &v);
+    if (rc) return rc;
+    solo[k] = v * g.n_sched;
+    cipc[k] = o[k] * g.n_sched;
+    if (solo[k] > 0.0) sum += cipc[k] / solo[k];
+  }
+  *cpv = sum > 0.0 ? 1.0 - 1.0 / sum : 0.0;
+  return KL_OK;
+}
+
 bool pruned(double pur_a, double mur_a, double pur_b, double mur_b, double ap, double am) {
   if (ap < 0.0 || am < 0.0) return false;
   return std::fabs(pur_a - pur_b) < ap && std::fabs(mur_a - mur_b) < am;
@@ -312,6 +344,16 @@ extern "C" int kl_model_pair(const kl_model_params* gp, const kl_profile* pa, co
     return KL_EINVAL;
   return model::pair(*gp, *pa, *pb, slots, (int)model_states, policy, fixed_a, cipc_a, cipc_b, cp, dT, solo_ipc,
                      best_a);
+}
+
+extern "C" int kl_model_phase(const kl_model_params* gp, const kl_profile* profiles, const uint32_t* slots,
+                              uint32_t n, uint32_t total_slots, uint32_t model_states, double* cipc_out,
+                              double* solo_out, double* cp_out) {
+  if (!gp || !profiles || !slots || !cipc_out || !solo_out || !cp_out || n < 1 || n > 4) return KL_EINVAL;
+  if (total_slots < 1 || total_slots > KL_MAX_SLOTS || (model_states != 2 && model_states != 3)) return KL_EINVAL;
+  const kl_profile* pp[4];
+  for (uint32_t k = 0; k < n; ++k) pp[k] = &profiles[k];
+  return model::phase(*gp, pp, slots, (int)n, total_slots, (int)model_states, cipc_out, solo_out, cp_out);
 }
 
 extern "C" int kl_count_pruned(const double* pur, const double* mur, uint32_t n, double ap, double am,

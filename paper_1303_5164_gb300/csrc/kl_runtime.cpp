@@ -38,6 +38,8 @@ namespace model {
 int pair(const kl_model_params& g, const kl_profile& pa, const kl_profile& pb, uint32_t slots, int states,
          uint32_t policy, uint32_t fixed_a, double* cA, double* cB, double* cpv, double* dT, double* solo,
          uint32_t* best_a);
+int phase(const kl_model_params& g, const kl_profile* const* pp, const uint32_t* slots, int n, uint32_t total,
+          int states, double* cipc, double* solo, double* cpv);
 bool pruned(double pur_a, double mur_a, double pur_b, double mur_b, double ap, double am);
 }  // namespace model
 }  // namespace kl
@@ -283,6 +285,7 @@ struct kl_runtime {
   bool table_valid = false;
   bool table_override = false;  // kl_set_cp_table: measured CPs instead of the model
   uint32_t table_slots = 0;     // slots per SM the cached table was computed for
+  int table_chain = -1;         // chain-lane type of the cached table (KL_CFG_PHASE_MODEL)
   double cp[KL_T_COUNT][KL_T_COUNT];
   uint32_t slots_a[KL_T_COUNT][KL_T_COUNT];
   uint32_t allowed[KL_T_COUNT][KL_T_COUNT];
@@ -330,10 +333,16 @@ void split_handle(kl_handle h, uint64_t* run, uint32_t* idx) {
 
 // CP table for every pair of types in `mask` (Section 4.4 model + Section 4.3
 // pruning). Cached until profiles, parameters or the type set change.
-int ensure_table(kl_runtime* rt, uint32_t mask, uint32_t S) {
+// chain: with KL_CFG_PHASE_MODEL, the multi-stage type the chain lane will run
+// beside every pair (-1: none); the table then holds each pair's CP as the
+// three-kernel phase the device runs (pair on S - chain_slots slots, that
+// type on the chain lane), at the split of the pair that maximises it.
+int ensure_table(kl_runtime* rt, uint32_t mask, uint32_t S, int chain = -1) {
   if (rt->table_override) return KL_OK;
   mask &= (1u << KL_T_MAIN_COUNT) - 1u;  // the planner pairs the co-scheduler's types only
-  const bool same = rt->table_valid && rt->table_slots == S;
+  const uint32_t cs = std::max(1u, std::min(rt->cfg.chain_slots, S > 1 ? S - 1 : 1u));
+  if (chain >= 0 && S < cs + 2) chain = -1;  // no room for a pair beside the lane
+  const bool same = rt->table_valid && rt->table_slots == S && rt->table_chain == chain;
   if (same && (rt->table_types & mask) == mask) return KL_OK;
   const uint32_t want = mask | (same ? rt->table_types : 0u);
   std::vector<double> a(S), b(S), c(S), d(S);
@@ -355,6 +364,21 @@ int ensure_table(kl_runtime* rt, uint32_t mask, uint32_t S) {
         if (rc) return rc;
         rt->cp[i][j] = c[best - 1];
         rt->slots_a[i][j] = best;
+        if (chain >= 0) {
+          const kl_profile* pp[3] = {&rt->prof[i], &rt->prof[j], &rt->prof[chain]};
+          double bestcp = -1e300;
+          for (uint32_t sa = 1; sa + cs < S; ++sa) {
+            const uint32_t sl[3] = {sa, S - cs - sa, cs};
+            double ci[3], so[3], cpv = 0.0;
+            rc = model::phase(rt->mp, pp, sl, 3, S, (int)rt->cfg.model_states, ci, so, &cpv);
+            if (rc) return rc;
+            if (cpv > bestcp + 1e-12) {
+              bestcp = cpv;
+              rt->cp[i][j] = cpv;
+              rt->slots_a[i][j] = sa;
+            }
+          }
+        }
         rt->allowed[i][j] = model::pruned(rt->prof[i].PUR, rt->prof[i].MUR, rt->prof[j].PUR, rt->prof[j].MUR,
                                           rt->cfg.alpha_p, rt->cfg.alpha_m)
                                 ? 0u
@@ -364,6 +388,7 @@ int ensure_table(kl_runtime* rt, uint32_t mask, uint32_t S) {
   }
   rt->table_types = want;
   rt->table_slots = S;
+  rt->table_chain = chain;
   rt->table_valid = true;
   return KL_OK;
 }
@@ -1014,7 +1039,21 @@ static int launch_locked(kl_runtime* rt) {
   // a resource-class CTA takes up to half an SM's registers: the co-scheduler
   // keeps two slots per SM beside it
   if (cls_mask && has_main) S = std::min<uint32_t>(S, 2u);
-  int rc = has_main && S >= 1 ? ensure_table(rt, mask, S) : KL_OK;
+  // KL_CFG_PHASE_MODEL: the multi-stage type with the most blocks pending is
+  // what the chain lane runs beside the pairs
+  int chain = -1;
+  if ((rt->cfg.flags & KL_CFG_PHASE_MODEL) && (rt->cfg.flags & KL_CFG_CHAIN_LANE)) {
+    uint64_t most = 0;
+    uint64_t per_type[KL_T_COUNT] = {0};
+    for (const Pending& p : rt->pending)
+      if (p.td.nstages > 1 && tn::resource_class(p.td.type) == tn::kClassMain) per_type[p.td.type] += p.td.total;
+    for (uint32_t t = 0; t < KL_T_MAIN_COUNT; ++t)
+      if (per_type[t] > most) {
+        most = per_type[t];
+        chain = (int)t;
+      }
+  }
+  int rc = has_main && S >= 1 ? ensure_table(rt, mask, S, chain) : KL_OK;
   if (rc) return rc;
   // device image: run state, tenants, the "plan first" phase
   RunDev& R = *rt->h_run;

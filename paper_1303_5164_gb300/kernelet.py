@@ -39,6 +39,7 @@ KL_CFG_LAZY_ARRIVAL = 32
 KL_CFG_RANDOM_PLAN = 64
 KL_CFG_LIGHT_BUILD = 128
 KL_CFG_DEEP_FILL = 256
+KL_CFG_PHASE_MODEL = 512
 
 P = C.c_void_p
 U32, U64, I32, F32, F64 = C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
@@ -213,6 +214,8 @@ SIGNATURES = [
                           C.POINTER(U64), U32, U32, U32, U32, F64, F64, C.POINTER(kl_phase),
                           C.POINTER(F64), U32, C.POINTER(U32), C.POINTER(F64)]),
     ("kl_count_pruned", C.c_int, [C.POINTER(F64), C.POINTER(F64), U32, F64, F64, C.POINTER(U32)]),
+    ("kl_model_phase", C.c_int, [C.POINTER(kl_model_params), C.POINTER(kl_profile), C.POINTER(U32), U32, U32,
+                                 U32, C.POINTER(F64), C.POINTER(F64), C.POINTER(F64)]),
     ("kl_run_noalloc", C.c_int, [C.POINTER(kl_kernel_desc), U32, C.POINTER(F64), C.POINTER(U32), P, U64,
                                  C.POINTER(I32)]),
 ]
@@ -271,6 +274,15 @@ def model_pair(params, pa, pb, slots: int, states: int = 3, policy: int = KL_RAT
                               ca, cb, cp, dT, solo, C.byref(best)), "kl_model_pair")
     return dict(cipc_a=list(ca), cipc_b=list(cb), cp=list(cp), dT=list(dT), solo=list(solo),
                 best_a=best.value)
+
+
+def model_phase(params, profiles, slots, total_slots: int, states: int = 3):
+    """kl_model_phase: (cipc per kernel, solo ipc per kernel, cp) of an n-kernel phase."""
+    n = len(profiles)
+    c, so, cp = (F64 * n)(), (F64 * n)(), F64()
+    check(lib().kl_model_phase(C.byref(params), _arr(kl_profile, profiles), _arr(U32, slots), n, total_slots, states,
+                               c, so, C.byref(cp)), "kl_model_phase")
+    return list(c), list(so), cp.value
 
 
 def plan(params, type_profiles, types, blocks, slots: int, states: int = 3,

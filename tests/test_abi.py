@@ -183,6 +183,22 @@ def test_model_pair_matches_oracle(K, seed):
         assert r["best_a"] == best.bA
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_model_phase_matches_oracle(K, seed):
+    # three kernels sharing the SM (a pair plus the chain lane's kernel), and
+    # a kernel with no slot at all
+    rng = np.random.default_rng(300 + seed)
+    ps = [_rand_prof(rng, f_u=bool(k % 2)) for k in range(3)]
+    for slots, total, states in (((1, 2, 1), 4, 3), ((2, 1, 1), 4, 2), ((1, 1, 2), 6, 3), ((2, 2, 0), 4, 3)):
+        ci, so, cp = K.model_phase(_mp(K), [_kp(K, p) for p in ps], list(slots), total, states)
+        oc, osolo, ocp = mk.phase_cp(ps, list(slots), total, GPU, three_state=states == 3)
+        assert np.allclose(ci, oc, rtol=1e-11, atol=1e-14)
+        assert np.allclose(so, osolo, rtol=1e-11)
+        assert np.isclose(cp, ocp, rtol=1e-10, atol=1e-13)
+    with pytest.raises(K.KLError):
+        K.model_phase(_mp(K), [_kp(K, p) for p in ps], [2, 2, 1], 4, 3)   # more slots than the SM has
+
+
 def test_count_pruned_table3(K):
     gold = os.path.join(ROOT, "tests", "golden")
     rows = [l.split() for l in open(os.path.join(gold, "c2050_pur_mur.txt")) if not l.startswith("#")]

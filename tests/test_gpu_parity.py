@@ -158,12 +158,18 @@ def _oracle_profiles(K, rt):
     return gpu
 
 
-@pytest.mark.parametrize("alpha", [None, (0.25, 0.12)])
+@pytest.mark.parametrize("alpha", [None, (0.25, 0.12), "refit"])
 def test_mix_alone_equals_in_mix_and_decisions_match_oracle(K, T, alpha):
     # alpha: pruning thresholds (alpha_p, alpha_m) of Section 4.3 on the device
     # planner and the oracle alike; with (0.25, 0.12) every pair of types
     # fewer than three apart below is pruned (their PUR and MUR gaps are both
-    # small), same-type pairs included
+    # small), same-type pairs included; "refit": the thresholds re-fit on
+    # GB300 from the testing kernels (profiles_gb300.json)
+    if alpha == "refit":
+        import json
+        import os
+        doc = json.load(open(os.path.join(os.path.dirname(K.__file__), "profiles_gb300.json")))
+        alpha = (doc["pruning"]["alpha_p"], doc["pruning"]["alpha_m"])
     from oracle import markov as mk
     from oracle import schedule as sc
     rng = np.random.default_rng(2)

@@ -190,6 +190,38 @@ def test_balanced_ratio_minimises_dT():
         assert 0.0 < e.cipcA <= ia + 1e-12 and 0.0 < e.cipcB <= ib + 1e-12
 
 
+# --------------------------------------------------------------------- phases of n kernels
+
+def test_phase_of_two_is_the_pair_model():
+    pA, pB = prof(0.2, L0=700, I=3000), prof(0.02, L0=300, I=900, f_u=0.4)
+    _, evals, (ia, ib) = mk.evaluate_pair(pA, pB, 4, GPU, three_state=True)
+    for e in evals:
+        ci, solo, cp = mk.phase_cp([pA, pB], [e.bA, e.bB], 4, GPU, three_state=True)
+        assert np.allclose(ci, [e.cipcA, e.cipcB], rtol=1e-13) and np.allclose(solo, [ia, ib], rtol=1e-13)
+        assert abs(cp - e.cp) < 1e-13
+        # a third kernel without a slot changes nothing
+        ci3, _, cp3 = mk.phase_cp([pA, pB, prof(0.3)], [e.bA, e.bB, 0], 4, GPU, three_state=True)
+        assert np.allclose(ci3[:2], ci, rtol=1e-13) and ci3[2] == 0.0 and abs(cp3 - cp) < 1e-13
+
+
+def test_identical_kernels_in_a_phase_have_no_profit():
+    # three copies of one kernel on 1, 1 and 2 slots are the kernel alone on
+    # all 4 (the chain lumps exactly): their IPCs split 1:1:2 and sum to the
+    # solo IPC, so CP = 1 - 1/1 = 0
+    p = prof(0.15, L0=500)
+    ci, solo, cp = mk.phase_cp([p, p, p], [1, 1, 2], 4, GPU)
+    assert abs(sum(ci) - solo[0]) < 1e-12 * solo[0]
+    assert abs(ci[0] - ci[1]) < 1e-12 and abs(ci[2] - 2 * ci[0]) < 1e-12
+    assert abs(cp) < 1e-12
+
+
+def test_phase_is_symmetric_in_its_kernels():
+    ps = [prof(0.25, L0=800), prof(0.01, L0=300, f_u=0.5), prof(0.1, L0=500)]
+    ci, _, cp = mk.phase_cp(ps, [1, 2, 1], 4, GPU, three_state=True)
+    ci2, _, cp2 = mk.phase_cp([ps[2], ps[0], ps[1]], [1, 1, 2], 4, GPU, three_state=True)
+    assert np.allclose([ci2[1], ci2[2], ci2[0]], ci, rtol=1e-12) and abs(cp - cp2) < 1e-12
+
+
 # --------------------------------------------------------------------- pruning (Table 3)
 
 def _read_table():
