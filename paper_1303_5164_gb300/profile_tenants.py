@@ -61,7 +61,9 @@ METRICS = ",".join([
 
 TYPE_OF_KERNEL = {f"native_kernel<{i}>": n for i, n in enumerate(
     ["gather", "blackscholes", "gemm_f32", "spmv_csr", "pchase", "triad", "hist256", "escape", "bitonic",
-     "matadd", "gemm_bf16", "tea", "sad", "stencil", "mriq"])}
+     "matadd", "gemm_bf16", "tea", "sad", "stencil", "mriq", "testmix"])}
+TYPE_OF_KERNEL.update({"gemm_bf16_plain_kernel": "gemm_bf16", "native_heavy_kernel<16>": "bs255",
+                       "native_heavy_kernel<17>": "hist1024", "native_heavy_kernel<18>": "gemm_f32_big"})
 
 # Types left out of the a0/b0 fit, with the reason (their errors are still
 # reported): the Markov model's warps are either ready or waiting on memory.
@@ -246,6 +248,8 @@ def main(argv=None):
     ap.add_argument("--mode", default="native", choices=["native", "cosched", "mix"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--copies", type=int, default=1,
+                    help="replicas of each kernel (shared inputs, own outputs) in one run or plain launch sequence")
     ap.add_argument("--latency", default=None, help="run the latency probe, write JSON here")
     ap.add_argument("--ingest", default=None, help="ncu CSV (raw page) to turn into profiles")
     ap.add_argument("--latency-json", default=None)
@@ -263,10 +267,12 @@ def main(argv=None):
     from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
     build.build()
     tens = [T.make(t, x) for t, x in zip(types, inputs)]
+    copies = {id(t): [t] + [t.replica() for _ in range(args.copies - 1)] for t in tens}
     rt = K.Runtime()
 
     def run(t):
-        rt.submit(t.type, t.args)
+        for c in copies[id(t)]:
+            rt.submit(c.type, c.args)
         if args.mode == "native":
             rt.launch_baseline(K.KL_BASE_SERIAL, 1)
         else:
