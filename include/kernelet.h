@@ -493,6 +493,18 @@ int kl_submit(kl_runtime* rt, const kl_kernel_desc* desc, kl_handle* out);
 int kl_submit_staged(kl_runtime* rt, const kl_kernel_desc* desc, kl_handle* out);
 int kl_publish(kl_runtime* rt);
 
+/* A burst of arrivals in one call (Algorithm 1, "a new kernel comes", for n
+ * kernels that arrive together): admits descs[0..n) in order, exactly as n
+ * kl_submit_staged calls followed by one kl_publish, and writes their handles
+ * to out[0..n) (host arrays of n entries). It stops at the first kernel that
+ * kl_submit would refuse: *n_done (host, may be NULL) = kernels admitted
+ * before it (those stay admitted and, while serving, are published), and the
+ * call returns that kernel's error; on success *n_done = n. Allowed while a
+ * batch run is in flight: the kernels join the pending set of the next
+ * kl_launch. KL_EINVAL on NULL rt, or on NULL descs / out with n > 0. */
+int kl_submit_batch(kl_runtime* rt, const kl_kernel_desc* descs, uint32_t n, kl_handle* out,
+                    uint32_t* n_done);
+
 /* Plan and start the pending set as one persistent co-scheduled launch on the
  * runtime's stream (Algorithm 1 over the whole set); returns without waiting.
  * The launch uses the smallest co-scheduler build that holds every pending
@@ -569,6 +581,15 @@ int kl_wait(kl_runtime* rt, kl_handle h, uint64_t timeout_ns);
  * kl_drain waits again). Returns the run's status (KL_OK, KL_EDEVICE_TIMEOUT,
  * KL_EOVERFLOW, ...); KL_ESTATE while serving. */
 int kl_drain(kl_runtime* rt, uint64_t timeout_ns);
+
+/* Wait for the run in flight (co-scheduled or plain launches) to end, up to
+ * timeout_ns (KL_ETIMEDOUT; the run continues), WITHOUT launching the pending
+ * set: kernels submitted while the run was in flight stay pending for the
+ * next kl_launch. This lets a caller overlap building the next batch with the
+ * current run (submit, then wait, then launch). Returns the finished run's
+ * status (KL_OK when no run was in flight and none has failed); KL_ESTATE
+ * while serving, KL_EINVAL on NULL. */
+int kl_wait_run(kl_runtime* rt, uint64_t timeout_ns);
 
 /* Per-kernel measurements of a finished or running kernel (host memory out):
  * submit, start and end times, slices pulled and blocks executed. The start

@@ -1001,6 +1001,22 @@ extern "C" int kl_submit_staged(kl_runtime* rt, const kl_kernel_desc* d, kl_hand
   return submit_impl(rt, d, out, false);
 }
 
+extern "C" int kl_submit_batch(kl_runtime* rt, const kl_kernel_desc* descs, uint32_t n, kl_handle* out,
+                               uint32_t* n_done) {
+  if (n_done) *n_done = 0;
+  if (!rt || (n && (!descs || !out))) return KL_EINVAL;
+  int rc = KL_OK;
+  uint32_t k = 0;
+  for (; k < n; ++k) {
+    rc = submit_impl(rt, &descs[k], &out[k], false);
+    if (rc) break;
+  }
+  if (n_done) *n_done = k;
+  // one publish for the whole burst (serving: one tail store, one re-plan)
+  const int pr = kl_publish(rt);
+  return rc ? rc : pr;
+}
+
 extern "C" int kl_publish(kl_runtime* rt) {
   if (!rt) return KL_EINVAL;
   std::lock_guard<std::mutex> lk(rt->mu);
@@ -1286,8 +1302,9 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     // dynamic shared memory of the largest type a serving run can receive
     const bool tc = (rt->cfg.flags & KL_CFG_SERVE_TC) != 0;
     uint32_t smem = tn::kMinCtaSmem;
+    // the types the launched build holds (resource-class variants never run in it)
     for (uint32_t t = 0; t < KL_T_COUNT; ++t)
-      if (tn::in_plain_build(t) || tc) smem = std::max(smem, tn::smem_bytes(t));
+      if (tn::in_plain_build(t) || (tc && tn::in_build(tn::kBuildFull, t))) smem = std::max(smem, tn::smem_bytes(t));
     if (!rc && cosched_launch(rt->sd_ring, rt->d_run, rt->sd_phases, rt->n_sm, rt->slots, smem,
                               tc ? tn::kBuildFull : tn::kBuildPlain, s) != 0)
       rc = KL_ECUDA;
@@ -1462,6 +1479,17 @@ extern "C" int kl_drain(kl_runtime* rt, uint64_t timeout_ns) {
   }
   if (rt->in_flight) {
     rc = wait_flight(rt, lk, timeout_ns);
+    if (rc == KL_ETIMEDOUT || rc == KL_ECUDA) return rc;
+  }
+  return rt->last.error;
+}
+
+extern "C" int kl_wait_run(kl_runtime* rt, uint64_t timeout_ns) {
+  if (!rt) return KL_EINVAL;
+  std::unique_lock<std::mutex> lk(rt->mu);
+  if (rt->serve_on) return KL_ESTATE;
+  if (rt->in_flight) {
+    const int rc = wait_flight(rt, lk, timeout_ns);
     if (rc == KL_ETIMEDOUT || rc == KL_ECUDA) return rc;
   }
   return rt->last.error;

@@ -189,6 +189,7 @@ SIGNATURES = [
     ("kl_submit", C.c_int, [P, C.POINTER(kl_kernel_desc), C.POINTER(U64)]),
     ("kl_submit_staged", C.c_int, [P, C.POINTER(kl_kernel_desc), C.POINTER(U64)]),
     ("kl_publish", C.c_int, [P]),
+    ("kl_submit_batch", C.c_int, [P, C.POINTER(kl_kernel_desc), U32, C.POINTER(U64), C.POINTER(U32)]),
     ("kl_launch", C.c_int, [P]),
     ("kl_serve_start", C.c_int, [P, C.c_int, U32, U64]),
     ("kl_serve_stop", C.c_int, [P, U64]),
@@ -197,6 +198,7 @@ SIGNATURES = [
     ("kl_poll", C.c_int, [P, U64, C.POINTER(C.c_int)]),
     ("kl_wait", C.c_int, [P, U64, U64]),
     ("kl_drain", C.c_int, [P, U64]),
+    ("kl_wait_run", C.c_int, [P, U64]),
     ("kl_get_stats", C.c_int, [P, U64, C.POINTER(kl_tenant_stats)]),
     ("kl_get_run_stats", C.c_int, [P, C.POINTER(kl_run_stats)]),
     ("kl_get_phases", C.c_int, [P, C.POINTER(kl_phase), U32, C.POINTER(U32)]),
@@ -327,6 +329,16 @@ def make_desc(type_: int, args, slice_blocks: int = 0, footprint: int = 0) -> kl
     return d
 
 
+def make_descs(items) -> "C.Array":
+    """Array of descriptors for kl_submit_batch from (type, args) pairs (or
+    (type, args, slice_blocks, footprint)); the args structs must outlive it."""
+    items = list(items)
+    arr = (kl_kernel_desc * len(items))()
+    for k, it in enumerate(items):
+        arr[k] = make_desc(*it)
+    return arr
+
+
 def config_default() -> kl_config:
     c = kl_config()
     check(lib().kl_config_default(C.byref(c)), "kl_config_default")
@@ -374,6 +386,15 @@ class Runtime:
     def publish(self):
         check(lib().kl_publish(self._h), "kl_publish")
 
+    def submit_batch(self, descs, n: int | None = None):
+        """kl_submit_batch of the first n descriptors of a make_descs array
+        (all by default); returns the handles (a ctypes array of n uint64)."""
+        n = len(descs) if n is None else n
+        out = (U64 * max(1, n))()
+        done = U32()
+        check(lib().kl_submit_batch(self._h, descs, n, out, C.byref(done)), "kl_submit_batch")
+        return out
+
     def submit_desc(self, desc: kl_kernel_desc) -> int:
         h = U64()
         check(lib().kl_submit(self._h, C.byref(desc), C.byref(h)), "kl_submit")
@@ -418,6 +439,10 @@ class Runtime:
 
     def drain(self, timeout_ns: int = 30_000_000_000) -> int:
         return lib().kl_drain(self._h, timeout_ns)
+
+    def wait_run(self, timeout_ns: int = 30_000_000_000) -> int:
+        """kl_wait_run: wait for the run in flight without launching the pending set."""
+        return lib().kl_wait_run(self._h, timeout_ns)
 
     def stats(self, h: int) -> kl_tenant_stats:
         s = kl_tenant_stats()

@@ -51,6 +51,9 @@ def test_errors_without_gpu(K):
     assert L.kl_create(C.byref(cfg), None, C.byref(out)) == K.KL_EINVAL
     assert L.kl_submit(None, None, None) == K.KL_EINVAL
     assert L.kl_drain(None, 0) == K.KL_EINVAL
+    assert L.kl_wait_run(None, 0) == K.KL_EINVAL
+    done = C.c_uint32(7)
+    assert L.kl_submit_batch(None, None, 0, None, C.byref(done)) == K.KL_EINVAL and done.value == 0
     # shape queries are host-only
     a = K.kl_args_triad(16, 32, 48, 3.0, 0, 3 * 4096 + 7)
     sh = K.tenant_shape(K.KL_T_TRIAD, a)

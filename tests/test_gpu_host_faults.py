@@ -12,7 +12,12 @@
   output, the unpublished one never runs (its output stays untouched) and
   ends in KL_ERROR, and the runtime serves again afterwards;
 * a staged burst becomes visible only at kl_publish (Algorithm 1: the burst
-  arrives at once and is planned once)."""
+  arrives at once and is planned once);
+* a batch submitted with kl_submit_batch while a run is in flight joins the
+  next run, not the running one: kl_wait_run returns with it still pending,
+  the next kl_launch runs it, and both batches match the oracle; a batch with
+  a bad descriptor in the middle admits the kernels before it and reports
+  how many."""
 import ctypes as C
 import threading
 import time
@@ -201,4 +206,48 @@ def test_staged_burst_runs_only_after_publish(K, T, mode):
     h = rt.submit(tens[0].type, tens[0].args, staged=True)
     rt.publish()
     assert rt.drain() == 0 and rt.poll(h) == K.KL_DONE
+    rt.close()
+
+
+def test_batch_submitted_during_a_run_joins_the_next_run(K, T):
+    import ctypes as C
+    names = ["blackscholes", "triad", "hist256", "bitonic", "spmv_csr", "gemm_f32"]
+    sizes = {"blackscholes": dict(n=50001), "triad": dict(n=200000), "hist256": dict(n=100003),
+             "bitonic": dict(log2n=14), "spmv_csr": dict(nrows=7000), "gemm_f32": dict(M=130, N=72, K=40)}
+    first = [("pchase", gen.gen_pchase(23, 0, **LONG))] + [
+        (nm, gen.gen_tenant(nm, 23, 1 + i, **sizes[nm])) for i, nm in enumerate(names)]
+    second = [(nm, gen.gen_tenant(nm, 24, i, **sizes[nm])) for i, nm in enumerate(names)]
+    t1 = [T.make(nm, x) for nm, x in first]
+    t2 = [T.make(nm, x) for nm, x in second]
+    _poison(t1 + t2)
+    rt = K.Runtime()
+    h1 = list(rt.submit_batch(K.make_descs((t.type, t.args) for t in t1)))
+    rt.launch()
+    d2 = K.make_descs((t.type, t.args) for t in t2)
+    h2 = list(rt.submit_batch(d2))            # the pointer chase keeps the first run busy meanwhile
+    assert len(set(h1 + h2)) == len(h1) + len(h2)
+    assert rt.poll(h1[0]) in (K.KL_RUNNING, K.KL_PENDING)
+    assert rt.wait_run() == 0
+    for h in h1:
+        assert rt.poll(h) == K.KL_DONE
+    for h, t in zip(h2, t2):
+        assert rt.poll(h) == K.KL_PENDING and rt.wait(h, 0) == K.KL_ESTATE
+        assert all(_still_poisoned(v) for v in t.fetch().values())
+    assert rt.wait_run() == 0                  # nothing in flight: returns at once, launches nothing
+    assert rt.poll(h2[0]) == K.KL_PENDING
+    rt.launch()
+    assert rt.wait_run() == 0
+    for h in h2:
+        assert rt.poll(h) == K.KL_DONE
+    for (nm, x), t in zip(first + second, t1 + t2):
+        X.check(nm, x, t.fetch(), X.expected(nm, x))
+
+    # a refused descriptor in the middle: the ones before it stay admitted
+    bad = K.make_descs((t.type, t.args) for t in t2[:3])
+    bad[1].type = 200
+    out = (C.c_uint64 * 3)()
+    done = C.c_uint32()
+    assert K.lib().kl_submit_batch(rt._h, bad, 3, out, C.byref(done)) == K.KL_EINVAL
+    assert done.value == 1 and out[0] != 0 and rt.poll(out[0]) == K.KL_PENDING
+    assert rt.drain() == 0 and rt.poll(out[0]) == K.KL_DONE
     rt.close()
