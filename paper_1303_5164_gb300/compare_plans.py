@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 COPIES = 8
 
 
-def run(out_path, mc=1000, mc_pure=200, reps=5):
+def run(out_path, mc=1000, mc_pure=200, reps=5, extra_flags=0):
     import torch
     import bench
     from workloads import gen
@@ -169,14 +169,22 @@ def run(out_path, mc=1000, mc_pure=200, reps=5):
            "model_table": {f"{a}+{b}": (cp_model[one[a].type * TC + one[b].type],
                                         sl_model[one[a].type * TC + one[b].type])
                            for a, b in itertools.combinations_with_replacement(types, 2)}}
-    for label, flags, n_mc in (("default_flags", None, mc), ("pure_pairs", 0, mc_pure)):
+    res["extra_flags"] = extra_flags
+    for label, flags, n_mc in (("default_flags", K.config_default().flags, mc), ("pure_pairs", 0, mc_pure)):
+        flags |= extra_flags
         rt = runtime(flags=flags)
         kern = mix_time(rt)
         rt.close()
         rt = runtime(flags=flags, table=(cp, sl))
         opt = mix_time(rt)
         rt.close()
-        base_flags = K.config_default().flags if flags is None else flags
+        phase = None
+        if flags & K.KL_CFG_CHAIN_LANE:
+            # Section 4.4 with the phase the device runs: pair + chain-lane kernel scored together
+            rt = runtime(flags=flags | K.KL_CFG_PHASE_MODEL)
+            phase = mix_time(rt)
+            rt.close()
+        base_flags = flags
         mcs = []
         for seed in range(1, n_mc + 1):
             rt = runtime(flags=base_flags | K.KL_CFG_RANDOM_PLAN, seed=seed)
@@ -189,6 +197,9 @@ def run(out_path, mc=1000, mc_pure=200, reps=5):
                       "mc_min_ms": mcs_sorted[0], "mc_median_ms": statistics.median(mcs),
                       "mc_max_ms": mcs_sorted[-1],
                       "mc_fraction_faster_than_kernelet": sum(x < k_med for x in mcs) / len(mcs),
+                      "kernelet_phase_model_median_ms": statistics.median(phase) if phase else None,
+                      "mc_fraction_faster_than_phase_model":
+                          sum(x < statistics.median(phase) for x in mcs) / len(mcs) if phase else None,
                       "mc_cdf_ms": [mcs_sorted[int(q * (len(mcs) - 1))] for q in
                                     (0.0, 0.01, 0.05, 0.1, 0.25, 0.5, 0.75, 0.9, 0.95, 0.99, 1.0)]}
         print(label, json.dumps({k: v for k, v in res[label].items() if k not in ("kernelet_ms", "opt_ms")}),
@@ -202,8 +213,9 @@ def main(argv=None):
     ap.add_argument("--out", required=True)
     ap.add_argument("--mc", type=int, default=1000)
     ap.add_argument("--mc-pure", type=int, default=200)
+    ap.add_argument("--extra-flags", type=int, default=0, help="kl_config.flags bits added to every arm")
     a = ap.parse_args(argv)
-    run(a.out, a.mc, a.mc_pure)
+    run(a.out, a.mc, a.mc_pure, extra_flags=a.extra_flags)
 
 
 if __name__ == "__main__":
