@@ -278,7 +278,9 @@ def _measured_peaks():
 
 
 PROFILES = os.path.join(ROOT, "paper_1303_5164_gb300", "profiles_gb300.json")
-TRAFFIC = os.path.join(ROOT, "profiles", "cosched_kernel_mix64_dram.txt")
+# DRAM bytes of one co-scheduler launch on a small case (one instance of each
+# mix type), with the factor that scales it to the bench's launch
+TRAFFIC = os.path.join(ROOT, "profiles", "cosched_kernel_mix_dram.txt")
 KERNEL_SOURCES = ["kl_cosched.cu", "tenants.cuh", "kl_internal.h"]
 
 
@@ -294,8 +296,9 @@ def kernel_source_hash() -> str:
 
 
 def _measured_traffic(workload: str):
-    """DRAM bytes per cosched_kernel launch from the committed ncu summary, or
-    None when it is missing, for another workload, or taken on other sources."""
+    """DRAM bytes per cosched_kernel launch of the bench's workload, from the
+    committed ncu summary of a smaller launch scaled by the units it processed,
+    or None when it is missing, for another workload, or taken on other sources."""
     if not os.path.exists(TRAFFIC):
         return None
     kv = {}
