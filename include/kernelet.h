@@ -325,13 +325,6 @@ typedef enum {
                                the most blocks pending), with the three-kernel
                                chain of kl_model_phase, at the pair's split that
                                maximises that phase's CP; off by default */
-#define KL_CFG_L2_BUDGET 1024u /* a kernel whose speed rests on a random-access
-                               working set that L2 can hold (the pointer chase:
-                               its N x 4-byte cycle) starts only while the working
-                               sets of such kernels already started, plus its own,
-                               fit half of the L2 (one may always run), so two
-                               L2-sized chases do not push each other out to DRAM
-                               latency; its slots take other work meanwhile */
 #define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their

@@ -140,23 +140,7 @@ __device__ __forceinline__ tn::Stage stage_at(const TenantDev& d, uint32_t type,
   return g < b0 ? tn::Stage{0u, 0u, b0} : tn::Stage{1u, b0, total};
 }
 
-// KL_CFG_L2_BUDGET: admit kernel d (its first slice) only while the L2 working
-// sets of the admitted, unfinished kernels plus its own fit the budget; the
-// first one is always admitted. One CTA admits a kernel (state 0 -> 1 -> 2);
-// another CTA trying meanwhile sees it blocked and tries again later.
-__device__ __noinline__ bool l2_admit(TenantDev& d, RunDev* R) {
-  if (atomicCAS(&d.l2_state, 0u, 1u) != 0u) return ld_relaxed(&d.l2_state) == 2u;
-  const uint32_t used = atomicAdd(&R->l2_used_kb, d.l2_kb);
-  if (used != 0u && (uint64_t)used + d.l2_kb > R->l2_budget_kb) {
-    atomicSub(&R->l2_used_kb, d.l2_kb);
-    st_release(&d.l2_state, 0u);
-    return false;
-  }
-  st_release(&d.l2_state, 2u);
-  return true;
-}
-
-__device__ __forceinline__ int try_pull(TenantDev* T, RunDev* R, int32_t t, uint32_t rank, uint32_t n_sm,
+__device__ __forceinline__ int try_pull(TenantDev* T, const RunDev* R, int32_t t, uint32_t rank, uint32_t n_sm,
                                         uint32_t& g0, uint32_t& g1) {
   TenantDev& d = tenant(T, R, (uint32_t)t);
   // serving: a phase read just before the slot was refilled names an older kernel
@@ -167,7 +151,6 @@ __device__ __forceinline__ int try_pull(TenantDev* T, RunDev* R, int32_t t, uint
   tn::Stage st = stage_at(d, d.type, n);
   if (st.begin > ld_relaxed(&d.done)) return kBlocked;  // previous stage still running
   if ((uint64_t)rank * n_sm >= (uint64_t)(st.end - n)) return kBlocked;
-  if (d.l2_kb != 0u && ld_relaxed(&d.l2_state) != 2u && !l2_admit(d, R)) return kBlocked;
   uint32_t a = atomicAdd(&d.next, d.slice);
   if (a >= total) return kExhausted;
   g0 = a;
@@ -470,8 +453,6 @@ __device__ __forceinline__ void complete_tenant(TenantDev& d, RunDev* R) {
   unsigned long long now = gtimer();
   d.t_end = now;
   __threadfence();
-  // its working set leaves the L2 budget (after t_end: a kernel admitted next starts later)
-  if (d.l2_kb != 0u && ld_relaxed(&d.l2_state) == 2u) atomicSub(&R->l2_used_kb, d.l2_kb);
   st_release(&d.status, KL_DONE);
   if (R->serve) {
     // the host reaps completions from the queue while the run goes on: the

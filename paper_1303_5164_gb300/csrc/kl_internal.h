@@ -55,12 +55,9 @@ struct alignas(128) TenantDev {
   uint32_t drained;               // 1 once every block has been handed out
   uint32_t status;                // kl_state
   uint32_t slices;                // slices pulled
-  uint32_t l2_state;              // L2 budget: 0 not started, 1 being admitted, 2 admitted
+  uint32_t pad1;
   unsigned long long t_start;     // globaltimer of the first pulled slice
   unsigned long long t_end;       // globaltimer when the last block finished
-  uint32_t l2_kb;                 // host-written: L2 working set in KiB (0 = not budgeted);
-                                  // on this line because the static one is full
-  uint32_t pad1;
 };
 static_assert(sizeof(TenantDev) == 256, "TenantDev layout");
 
@@ -142,10 +139,8 @@ struct alignas(128) RunDev {
   // ---- resource classes (static, host-written)
   uint32_t n_sm;                      // SMs of the device (the grid may carry extra CTAs)
   uint32_t quota_exit;                // 1: main CTAs past `slots` on their SM exit at once
-  uint32_t l2_budget_kb;              // KL_CFG_L2_BUDGET: half of the L2, in KiB
   // ---- resource classes (dynamic, zero at launch)
   uint32_t cls_ctas[4];               // CTAs of class c that found work (index 0 unused)
-  uint32_t l2_used_kb;                // L2 working sets of the admitted, unfinished kernels
 };
 
 // One device-side copy (kl_cosched.cu, stage_copy): dst and src are

@@ -252,7 +252,6 @@ struct kl_runtime {
   int device = 0;
   cudaStream_t stream = nullptr;
   uint32_t n_sm = 0, slots = 0, occupancy = 0;
-  uint32_t l2_budget_kb = 0;   // KL_CFG_L2_BUDGET: half of the device's L2, in KiB
   uint32_t slots_light = 0;   // CTAs per SM of the light build (0: not used)
   uint32_t flight_slots = 0;  // CTAs per SM of the in-flight / last run
   uint32_t cap = 0, cap_phases = 0;
@@ -853,8 +852,6 @@ extern "C" int kl_create(const kl_config* cfg_in, void* cuda_stream, kl_runtime*
   int v = 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, cfg.device) != cudaSuccess) goto fail_cuda;
   rt->n_sm = (uint32_t)std::min(v, kMaxSM);
-  if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, cfg.device) != cudaSuccess) goto fail_cuda;
-  rt->l2_budget_kb = (uint32_t)((uint64_t)v / 2u / 1024u);
   {
     int occ = 0;
     // the tensor-core build reaches the same residency: its CTAs give up the
@@ -981,8 +978,6 @@ static int submit_impl(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out, 
   td.nstages = sh.nstages;
   td.blocks0 = sh.grid[0];
   memcpy(td.args, d->args, d->args_size);
-  if (rt->cfg.flags & KL_CFG_L2_BUDGET)
-    td.l2_kb = (uint32_t)std::min<uint64_t>((tn::l2_working_set(d->type, d->args) + 1023u) / 1024u, 0xffffffffu);
   if (rt->serve_on) return serve_publish(rt, td, d->footprint_bytes, out, publish);
   if (rt->pending.size() >= rt->cap) return KL_EAGAIN;
   if (rt->cfg.mem_cap_bytes && rt->pending_footprint + d->footprint_bytes > rt->cfg.mem_cap_bytes) return KL_EAGAIN;
@@ -1094,7 +1089,6 @@ static int launch_locked(kl_runtime* rt) {
   memcpy(R.slots_a, rt->slots_a, sizeof(R.slots_a));
   memcpy(R.allowed, rt->allowed, sizeof(R.allowed));
   R.n_sm = rt->n_sm;
-  R.l2_budget_kb = rt->l2_budget_kb;
   R.quota_exit = (cls_mask && has_main) ? 1u : 0u;
   // resource classes present in the run, each run by its class kernel with
   // two CTAs per SM (they take the room the co-scheduler's two slots leave)
@@ -1277,7 +1271,6 @@ extern "C" int kl_serve_start(kl_runtime* rt, int mode, uint32_t nstreams, uint6
     memset(&R, 0, sizeof(R));
     R.slots = rt->slots;
     R.n_sm = rt->n_sm;
-    R.l2_budget_kb = rt->l2_budget_kb;
     R.max_phases = rt->s_phase_slots;
     R.n_types = KL_T_COUNT;
     R.wait_limit_ns = rt->cfg.device_wait_limit_ns;

@@ -153,16 +153,6 @@ __host__ __device__ inline uint64_t total_blocks(uint32_t type, const void* a) {
   return t;
 }
 
-// Bytes of the working set a kernel reads at random and keeps reading for
-// its whole run, when its arguments give it exactly: the pointer chase's
-// cycle (every hop a dependent load anywhere in it). Held in L2, a hop costs
-// the L2 latency; pushed out by another such kernel, the DRAM latency. 0 for
-// every other type (streams, tiles, or a size the arguments do not give).
-__host__ __device__ inline uint64_t l2_working_set(uint32_t type, const void* a) {
-  if (type == KL_T_PCHASE) return 4ull * ((const kl_args_pchase*)a)->N;
-  return 0;
-}
-
 // Stage containing cumulative block g (g < total).
 __host__ __device__ inline Stage stage_of(uint32_t type, const void* a, uint32_t g) {
   if (type == KL_T_HIST256 || type == KL_T_HIST1024) {

@@ -40,7 +40,6 @@ KL_CFG_RANDOM_PLAN = 64
 KL_CFG_LIGHT_BUILD = 128
 KL_CFG_DEEP_FILL = 256
 KL_CFG_PHASE_MODEL = 512
-KL_CFG_L2_BUDGET = 1024
 
 P = C.c_void_p
 U32, U64, I32, F32, F64 = C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
