@@ -965,12 +965,17 @@ __device__ __forceinline__ void bitonic_tile(uint32_t* t, uint32_t tile_n, uint6
 // index r then corresponds to a compare distance, so four consecutive levels
 // of the network run in registers between shared-memory exchanges:
 //   pattern 0: i = t + 256 r                       distances 2048, 1024, 512, 256
-//   pattern 1: i = (t/16) 256 + t%16 + 16 r        distances 128, 64, 32, 16
+//   pattern 1: i = t%16 + 16 r + thread bits 4, 5, 6, 7 as tile bits 9, 8, 10, 11
+//                                                   distances 128, 64, 32, 16
 //   pattern 2: i = 16 t + r                        distances 8, 4, 2, 1
+// In pattern 1 a warp's two halves are 512 words apart, 16 banks once the
+// tile is padded by one word per 32 (tpad): every exchange is free of bank
+// conflicts (with thread bit 4 as tile bit 8 the halves were 8 banks apart,
+// two-way conflicts on a third of the shared-memory traffic).
 template <int PAT>
 __device__ __forceinline__ uint32_t bt_elem(uint32_t t, uint32_t r) {
   if (PAT == 0) return t + 256u * r;
-  if (PAT == 1) return ((t >> 4) << 8) + (t & 15u) + 16u * r;
+  if (PAT == 1) return (t & 15u) + 16u * r + (((t >> 4) & 1u) << 9) + (((t >> 5) & 1u) << 8) + ((t >> 6) << 10);
   return 16u * t + r;
 }
 
