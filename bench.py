@@ -330,6 +330,7 @@ def _load_profiles(K, path=PROFILES):
                 setattr(p, k, float(e[k]))
             p.warps_per_block = int(e.get("warps_per_block", 8))
             p.slice_blocks = int(d.get("slices", {}).get(name, 0))
+            p.slice_blocks_alone = int(d.get("slice_autotune_alone", {}).get("slices", {}).get(name, 0))
             p.valid = 1
         profs.append(p)
     return profs, d

@@ -369,9 +369,12 @@ typedef struct {
     uint32_t warps_per_block;
     uint32_t valid;         /* 0 = no profile for this type                      */
     uint32_t slice_blocks;  /* blocks per slice for this type (Section 4.1: the
-                               smallest slice whose overhead is within p%);
-                               0 = the runtime's built-in size               */
-    uint32_t pad;
+                               smallest slice whose overhead is within p%,
+                               measured with several kernels of the type in
+                               one launch); 0 = the runtime's built-in size  */
+    uint32_t slice_blocks_alone; /* the same rule with one kernel alone: the
+                               least a slice shrinks to when a run has too few
+                               slices for its CTAs (0 = 1 block)             */
 } kl_profile;
 
 typedef struct {

@@ -10,7 +10,13 @@ assumes the overhead falls as slices grow; here it does not always (very
 large slices unbalance the SMs), so T_ns is the fastest of the measured runs,
 and the chosen size is the smallest with T_s / T_ns - 1 <= p.
 
-    python -m paper_1303_5164_gb300.autotune --out slices.json [--p 0.02]
+With --copies N the kernel runs as N copies in one launch (the same inputs,
+their own outputs), as it does in a co-scheduled run, where other kernels'
+slices fill the slots one kernel leaves idle between its stages and at its
+end; alone, a kernel with stage barriers favours slices that spread each
+stage over every slot, in company the per-slice scheduling cost counts more.
+
+    python -m paper_1303_5164_gb300.autotune --out slices.json [--p 0.02] [--copies 8]
 """
 from __future__ import annotations
 
@@ -32,7 +38,7 @@ def choose_slice(times, p):
     return min(c for c in times if times[c] / tns - 1.0 <= p)
 
 
-def tune(types, p=0.02, reps=3, seed=6):
+def tune(types, p=0.02, reps=3, seed=6, copies=1):
     import torch
     from workloads import gen
     from paper_1303_5164_gb300 import build, kernelet as K, tenants as T
@@ -43,23 +49,25 @@ def tune(types, p=0.02, reps=3, seed=6):
     c.flags &= ~K.KL_CFG_LIGHT_BUILD
     rt = K.Runtime(c)
     n_sm = rt.model_params().n_sm
-    out = {"p": p, "n_sm": n_sm, "slices": {}, "times_us": {}, "overhead": {}, "slots_per_sm": {}}
+    out = {"p": p, "n_sm": n_sm, "copies": copies, "slices": {}, "times_us": {}, "overhead": {}, "slots_per_sm": {}}
     for i, ty in enumerate(types):
         inp = gen.gen_tenant(ty, seed, i, **T.SIZES_ALL[ty])
         t = T.make(ty, inp)
+        group = [t] + [t.replica() for _ in range(copies - 1)]
         sh = t.shape()
         rt.submit(t.type, t.args)  # slots per SM of the build this type runs in
         rt.launch()
         assert rt.drain() == 0
         S = rt.run_stats().slots_per_sm
         stage_blocks = int(sh.grid[0]) if ty != "hist256" else int(sh.total_blocks - 1)
-        ref = max(1, math.ceil(stage_blocks / (n_sm * S)))
+        ref = max(1, math.ceil(copies * stage_blocks / (n_sm * S)))
         cands = sorted({c for c in (1, 2, 4, 8, 16, 32, 64) if c <= stage_blocks} | {ref})
 
         def run(sl):
             best = float("inf")
             for _ in range(reps + 1):
-                rt.submit(t.type, t.args, slice_blocks=sl)
+                for x in group:
+                    rt.submit(x.type, x.args, slice_blocks=sl)
                 rt.launch()
                 assert rt.drain() == 0
                 best = min(best, rt.run_stats().kernel_ns / 1e3)
@@ -73,7 +81,7 @@ def tune(types, p=0.02, reps=3, seed=6):
         out["overhead"][ty] = round(times[chosen] / tns - 1.0, 4)
         out["slots_per_sm"][ty] = S
         print(ty, "ref", ref, "chosen", chosen, out["times_us"][ty], flush=True)
-        del t
+        del t, group
         torch.cuda.empty_cache()
     rt.close()
     return out
@@ -85,8 +93,9 @@ def main(argv=None):
     ap.add_argument("--p", type=float, default=0.02)
     ap.add_argument("--types", default="gemm_f32,spmv_csr,blackscholes,pchase,triad,hist256,escape,bitonic,gather,"
                                        "tea,sad,stencil,mriq")
+    ap.add_argument("--copies", type=int, default=1, help="copies of the kernel in each timed launch")
     a = ap.parse_args(argv)
-    res = tune(a.types.split(","), a.p)
+    res = tune(a.types.split(","), a.p, copies=a.copies)
     with open(a.out, "w") as f:
         json.dump(res, f, indent=1)
 

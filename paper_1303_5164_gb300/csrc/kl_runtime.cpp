@@ -219,6 +219,8 @@ struct Pending {
   uint64_t footprint;
   uint64_t t_submit;
   kl_handle handle;
+  bool caller_slice;     // the descriptor set slice_blocks (never resized)
+  uint32_t slice_alone;  // the least its slice shrinks to (the type's alone-tuned slice)
 };
 
 struct Record {
@@ -987,6 +989,8 @@ static int submit_impl(kl_runtime* rt, const kl_kernel_desc* d, kl_handle* out, 
   p.footprint = d->footprint_bytes;
   p.t_submit = now_ns();
   p.handle = make_handle(rt->run_id, p.td.index);
+  p.caller_slice = d->slice_blocks != 0;
+  p.slice_alone = std::max(1u, rt->prof[d->type].slice_blocks_alone);
   rt->pending.push_back(p);
   rt->pending_footprint += d->footprint_bytes;
   *out = p.handle;
@@ -1096,8 +1100,28 @@ static int launch_locked(kl_runtime* rt) {
   uint32_t ncls = 0;
   for (int c = 1; c < tn::kNumClasses; ++c)
     if ((cls_mask >> c) & 1u) cls_list[ncls++] = c;
+  // Slices are tuned with several kernels of a type sharing the GPU; a run of
+  // few or small kernels could then hand out too few slices to balance its
+  // CTAs. Slices the run can hand out at once (a multi-stage kernel counts two
+  // stages: the others keep the slots busy at its barriers), summed over the
+  // co-scheduler's kernels: below four per CTA, the slices the caller did not
+  // set shrink by the missing factor, but never below the type's alone-tuned
+  // slice (the paper's rule for a kernel without company).
+  uint32_t shrink = 1;
+  if (has_main) {
+    uint64_t avail = 0;
+    for (const Pending& p : rt->pending) {
+      if (tn::resource_class(p.td.type) != tn::kClassMain) continue;
+      const uint64_t per_stage = std::max<uint64_t>(1u, p.td.total / std::max(1u, p.td.nstages));
+      avail += (per_stage + p.td.slice - 1) / p.td.slice * std::min(2u, std::max(1u, p.td.nstages));
+    }
+    const uint64_t want = 4ull * rt->n_sm * S;
+    if (avail < want) shrink = (uint32_t)((want + avail - 1) / avail);
+  }
   for (uint32_t i = 0; i < n; ++i) {
     TenantDev td = rt->pending[i].td;
+    if (shrink > 1 && !rt->pending[i].caller_slice)
+      td.slice = std::max(std::min(td.slice, rt->pending[i].slice_alone), td.slice / shrink);
     td.slice = clamp_slice(rt, td.slice, td.total);
     rt->h_tenants[i] = td;
   }

@@ -142,7 +142,7 @@ class kl_config(C.Structure):
 class kl_profile(C.Structure):
     _fields_ = [("R_m", F64), ("f_u", F64), ("m_c", F64), ("m_u", F64), ("L0", F64),
                 ("I_block", F64), ("PUR", F64), ("MUR", F64), ("warps_per_block", U32),
-                ("valid", U32), ("slice_blocks", U32), ("pad", U32)]
+                ("valid", U32), ("slice_blocks", U32), ("slice_blocks_alone", U32)]
 
 
 class kl_model_params(C.Structure):
