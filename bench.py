@@ -502,6 +502,7 @@ def e2e_leg(K, T, rt, tens, names, inputs, stream, local, world, steps, barrier)
     ev_done = [torch.cuda.Event(), torch.cuda.Event()]   # compute on set b finished
     ev_out = [torch.cuda.Event(), torch.cuda.Event()]    # outputs of set b downloaded
     spans = {"upload": [], "compute": [], "download": []}
+    timeline = []
 
     def upload(b):
         s_in.wait_event(ev_done[b])          # the previous run on set b no longer reads its inputs
@@ -557,6 +558,11 @@ def e2e_leg(K, T, rt, tens, names, inputs, stream, local, world, steps, barrier)
             stream.wait_event(ev_out[b])
         e1.record(stream)
         barrier()
+        # where each step's spans sit on the run's clock (ms from its start)
+        timeline.clear()
+        for k in range(min(nsteps, 6)):
+            timeline.append({n: [round(e0.elapsed_time(v[k][0]), 2), round(e0.elapsed_time(v[k][1]), 2)]
+                             for n, v in spans.items() if k < len(v)})
         return max_over_ranks(e0.elapsed_time(e1) / nsteps, world, "cuda")
 
     run(2)
@@ -587,6 +593,7 @@ def e2e_leg(K, T, rt, tens, names, inputs, stream, local, world, steps, barrier)
     return {"value": job_value(n, world, ms), "unit": "kernels/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms,
             "step_ms_median": {k: round(v, 3) for k, v in per.items()},
+            "timeline_ms": timeline,
             "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs,
             "host_numa_node": numa_node, "host_cores_bound": numa_cores,
             "how": "public API (kl_submit_batch/kl_launch/kl_drain) on pinned host buffers; uploads and downloads on "

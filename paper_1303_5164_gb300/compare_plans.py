@@ -77,8 +77,11 @@ def run(out_path, mc=1000, mc_pure=200, reps=5, extra_flags=0):
         order += [(b, copies[b][COPIES + k if a == b else k]) for k in range(COPIES)]
         best = None
         for _ in range(2):
+            # slices small enough that blocks finish inside every phase: the
+            # alone-tuned sizes (the run-level table hands a few copies one
+            # slice per CTA, and a phase would then count no finished block)
             for _, t in order:
-                rt.submit(t.type, t.args)
+                rt.submit(t.type, t.args, slice_blocks=int(profs[t.type].slice_blocks_alone))
             rt.launch()
             assert rt.drain() == 0
             ph = rt.phases()
@@ -117,7 +120,7 @@ def run(out_path, mc=1000, mc_pure=200, reps=5, extra_flags=0):
         solo[a] = (v[0] + v[1]) if v else None
     cp_meas = {}
     for (a, b, sa), v in meas.items():
-        if v and solo[a] and solo[b]:
+        if v and solo[a] and solo[b] and v[0] / solo[a] + v[1] / solo[b] > 0:
             cp_meas[(a, b, sa)] = 1.0 - 1.0 / (v[0] / solo[a] + v[1] / solo[b])
     # OPT table: each type pair at its best measured split (both orientations)
     TC = K.KL_T_COUNT
