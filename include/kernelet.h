@@ -324,7 +324,7 @@ typedef enum {
                                chain lane's kernel (the multi-stage type with
                                the most blocks pending), with the three-kernel
                                chain of kl_model_phase, at the pair's split that
-                               maximises that phase's CP; off by default */
+                               maximises that phase's CP; default on */
 #define KL_CFG_CHAIN_LANE 4u /* while kernels with more than one stage (chains of
                                dependent grids) are pending outside the current
                                co-schedule, the last slot of every SM takes their

@@ -775,7 +775,7 @@ extern "C" int kl_config_default(kl_config* c) {
   c->alpha_p = -1.0;
   c->alpha_m = -1.0;
   c->flags = KL_CFG_BACKFILL | KL_CFG_FILL_TYPES | KL_CFG_CHAIN_LANE | KL_CFG_WIDE_FILL | KL_CFG_LIGHT_BUILD |
-             KL_CFG_DEEP_FILL;
+             KL_CFG_DEEP_FILL | KL_CFG_PHASE_MODEL;
   c->chain_slots = 2;
   return KL_OK;
 }

@@ -177,7 +177,10 @@ def test_mix_alone_equals_in_mix_and_decisions_match_oracle(K, T, alpha):
     rng.shuffle(order)
     inps = [gen.gen_tenant(nm, 2, i, **MIX_SMALL[nm]) for i, nm in enumerate(order)]
     ap, am = alpha if alpha else (-1.0, -1.0)
-    rt = _runtime(K, slots_per_sm=4, alpha_p=ap, alpha_m=am)
+    # the pair model of Algorithm 1's FindCoSchedule (the phase model scores
+    # pairs with the chain-lane kernel; its decisions are checked below)
+    rt = _runtime(K, slots_per_sm=4, alpha_p=ap, alpha_m=am,
+                  flags=K.config_default().flags & ~K.KL_CFG_PHASE_MODEL)
     # known model inputs on both sides
     profs = []
     for t in range(K.KL_T_COUNT):
@@ -355,7 +358,7 @@ def test_claim_ahead_counts_every_slice_once(K, T):
     rt.close()
 
 
-@pytest.mark.parametrize("planner", ["random", "table"])
+@pytest.mark.parametrize("planner", ["random", "table", "phase"])
 def test_other_planners_keep_results(K, T, planner):
     # the MC comparison's random plans and an overridden CP table change only
     # the order and sharing of kernels: every result still equals the oracle
@@ -365,6 +368,9 @@ def test_other_planners_keep_results(K, T, planner):
     if planner == "random":
         c.flags |= K.KL_CFG_RANDOM_PLAN
         c.plan_seed = 7
+    if planner == "phase":
+        c.flags |= K.KL_CFG_PHASE_MODEL | K.KL_CFG_CHAIN_LANE
+        c.alpha_p = c.alpha_m = -1.0   # no pruning: every pair of pending types is a candidate
     rt = K.Runtime(c)
     if planner == "table":
         n = K.KL_T_COUNT
@@ -380,6 +386,32 @@ def test_other_planners_keep_results(K, T, planner):
     for (nm, x), t, h in zip(inps, tens, hs):
         assert rt.poll(h) == K.KL_DONE
         X.check(nm, x, t.fetch(), X.expected(nm, x))
+    if planner == "phase":
+        # every device decision is the largest-CP pair of pending kernel types
+        # (the lowest kernel of each type) in the table the runtime reports:
+        # the phase model's table, scored with the chain-lane kernel
+        cp, sa, _ = rt.cp_table()
+        n = K.KL_T_COUNT
+        for p in ph[1:-1]:
+            if p.B < 0:
+                continue
+            pend = [i for i in range(len(tens)) if (p.pending_mask >> i) & 1]
+            low = {}
+            for i in pend:
+                low.setdefault(tens[i].type, []).append(i)
+            cands = []
+            for ta in low:
+                for tb in low:
+                    if ta < tb:
+                        i, j = sorted((low[ta][0], low[tb][0]))
+                    elif ta == tb and len(low[ta]) > 1:
+                        i, j = low[ta][0], low[ta][1]
+                    else:
+                        continue
+                    cands.append(cp[tens[i].type * n + tens[j].type])   # (lower index, higher index)
+            best = max(cands)
+            got = cp[tens[p.A].type * n + tens[p.B].type]
+            assert got >= best - 1e-12, (p.A, p.B, got, best)
     if planner == "table":
         rt.set_cp_table(None)
     rt.close()
