@@ -18,6 +18,7 @@
 from __future__ import annotations
 
 import argparse
+import json
 import os
 import sys
 
@@ -250,6 +251,9 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--copies", type=int, default=1,
                     help="replicas of each kernel (shared inputs, own outputs) in one run or plain launch sequence")
+    ap.add_argument("--time", action="store_true",
+                    help="print each type's device time per kernel (CUDA events around the run, divided by "
+                         "--copies; median of --reps runs after the warm-up) and, for the GEMMs, TFLOP/s")
     ap.add_argument("--latency", default=None, help="run the latency probe, write JSON here")
     ap.add_argument("--ingest", default=None, help="ncu CSV (raw page) to turn into profiles")
     ap.add_argument("--latency-json", default=None)
@@ -290,13 +294,24 @@ def main(argv=None):
             raise RuntimeError(f"mix: {K.lib().kl_strerror(rc).decode()}")
 
     # a warm-up pass first (skip it in the profiler with -s)
+    times = {t.name: [] for t in tens}
     for r in range(1 + args.reps):
         if args.mode == "mix":
             run_mix()
         else:
             for t in tens:
                 run(t)
+                if r > 0:
+                    times[t.name].append(rt.run_stats().kernel_ns / 1e3 / len(copies[id(t)]))
         torch.cuda.synchronize()
+    if args.time and args.mode != "mix":
+        import statistics
+        for t, inp in zip(tens, inputs):
+            us = statistics.median(times[t.name])
+            line = {"type": t.name, "mode": args.mode, "copies": len(copies[id(t)]), "us_per_kernel": round(us, 2)}
+            if t.name in ("gemm_bf16", "gemm_f32", "gemm_f32_big"):
+                line["tflops"] = round(2.0 * int(inp["M"]) * int(inp["N"]) * int(inp["K"]) / (us * 1e-6) / 1e12, 1)
+            print(json.dumps(line), flush=True)
     rt.close()
     print("profiled:", ",".join(types), args.mode)
 
