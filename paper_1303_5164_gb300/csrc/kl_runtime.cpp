@@ -1056,6 +1056,7 @@ static int launch_locked(kl_runtime* rt) {
   if (all_light && !cls_mask && (rt->cfg.flags & KL_CFG_LIGHT_BUILD) && rt->slots_light && !rt->table_override)
     build = tn::kBuildLight;
   uint32_t S = build == tn::kBuildLight ? rt->slots_light : rt->slots;
+  const uint32_t S_build = S;
   // a resource-class CTA takes up to half an SM's registers: the co-scheduler
   // keeps two slots per SM beside it
   if (cls_mask && has_main) S = std::min<uint32_t>(S, 2u);
@@ -1165,7 +1166,22 @@ static int launch_locked(kl_runtime* rt) {
     rc = cuda_ok(cudaStreamWaitEvent(rt->side[q], rt->ev_fork, 0));
     if (!rc && class_launch(cls_type[cls_list[q]], rt->d_tenants, rt->d_run, 2u * rt->n_sm, rt->side[q]) != 0)
       rc = KL_ECUDA;
-    if (!rc) rc = cuda_ok(cudaEventRecord(rt->side_join[q], rt->side[q]));
+    if (!rc && q > 0) rc = cuda_ok(cudaEventRecord(rt->side_join[q], rt->side[q]));
+  }
+  // The room the class kernels held goes back to the co-scheduler when they
+  // are all done: behind them on the first side stream, the quota that made
+  // extra co-scheduler CTAs leave is lifted and a second grid of the
+  // co-scheduler joins the same run (its CTAs take the freed slots and pull
+  // from the same plan; if the run has ended they leave at once).
+  if (!rc && ncls) {
+    for (uint32_t q = 1; q < ncls && !rc; ++q) rc = cuda_ok(cudaStreamWaitEvent(rt->side[0], rt->side_join[q], 0));
+    if (!rc && has_main && S_build > S) {
+      rc = cuda_ok(cudaMemsetAsync(&rt->d_run->quota_exit, 0, sizeof(uint32_t), rt->side[0]));
+      if (!rc && cosched_launch(rt->d_tenants, rt->d_run, rt->d_phases, rt->n_sm, S_build - S, smem, build,
+                                rt->side[0], 0u) != 0)
+        rc = KL_ECUDA;
+    }
+    if (!rc) rc = cuda_ok(cudaEventRecord(rt->side_join[0], rt->side[0]));
   }
   for (uint32_t q = 0; q < ncls && !rc; ++q) rc = cuda_ok(cudaStreamWaitEvent(s, rt->side_join[q], 0));
   if (!rc) rc = cuda_ok(cudaEventRecord(rt->ev_k1, s));
