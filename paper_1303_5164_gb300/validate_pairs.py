@@ -46,7 +46,11 @@ def _profiles(K):
             for k in ("R_m", "f_u", "m_c", "m_u", "L0", "I_block", "PUR", "MUR"):
                 setattr(p, k, float(e[k]))
             p.warps_per_block = 8
-            p.slice_blocks = int(doc.get("slices", {}).get(name, 0))
+            # steady-state pair rates are read between phases: the alone-tuned
+            # slices, small enough that blocks finish inside every phase (the
+            # table tuned in company hands 8 copies one slice per CTA)
+            alone = doc.get("slice_autotune_alone", {}).get("slices", {})
+            p.slice_blocks = int(alone.get(name, doc.get("slices", {}).get(name, 0)))
             p.valid = 1
         profs.append(p)
     return profs, doc
